@@ -1,0 +1,343 @@
+"""Benchmark: lost 16x16 blocks concealed per second on one GB300.
+
+Workload (default): 16 synthetic 1920x1080 luma frames, per-frame i.i.d.
+block-loss rate U(5%, 50%), K = 200 iterations, rho = 0.7, delta = 0.2,
+gamma = 0.5, optimized processing order (Algorithm 1), all frames in one
+persistent launch.  A step is one pass of the whole hot path over the batch:
+block-loss maps, processing-order planning, extrapolation of every lost
+block, 8-bit output.  Inputs are resident in HBM when a step starts; the L2
+is flushed (a 256 MiB write) between timed steps, outside the timed events.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on
+the host cores instead (bounded sample of the same workload).
+Multi-GPU (torchrun): replicas, one batch per rank, no collective on the
+data path; the rank times are max-reduced.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import fse_synth  # noqa: E402
+
+METRIC = "lost 16x16 blocks concealed/s"
+UNIT = "blocks/s"
+K_ITERS = 200
+PARAMS = dict(rho=0.7, delta=0.2, gamma=0.5)
+FRAMES = 16
+# shared-memory traffic of the iteration loop per block and iteration: the
+# whole 64x64 complex FP32 weight spectrum W (4096 x 8 bytes)
+SMEM_BYTES_PER_ITER = 4096 * 8
+FLOP_PER_ITER = 4096 * 11  # complex multiply-subtract (8) + |R|^2 (3)
+SMS = 152
+SMEM_BYTES_PER_CLK = 128
+FP32_LANES = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=FRAMES)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(frames: int):
+    return fse_synth.workload_batch_1080p(frames)
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on the host cores: each step conceals a bounded
+    sample of the workload (the top 256 rows = 16 block rows of one frame)."""
+    import oracle
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    frames = make_workload(args.frames)
+    threads = oracle.max_threads()
+    samples = []
+    for i in range(args.warmup + args.steps):
+        img, mask = frames[i % len(frames)]
+        samples.append((np.ascontiguousarray(img[:256]), np.ascontiguousarray(mask[:256])))
+    times, blocks = [], 0
+    for i, (img, mask) in enumerate(samples):
+        t0 = time.perf_counter()
+        _, _, gob = oracle.conceal_frame(img, mask, iters=K_ITERS, order=oracle.ORDER_OPTIMIZED,
+                                         threads=threads, **PARAMS)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            blocks += int((gob >= 0).sum())
+    total = sum(times)
+    value = blocks / total
+    sample = (f"top 256 rows (16 block rows) of one 1920x1080 frame per step, frames "
+              f"0..{args.steps - 1}; {blocks} lost blocks over {args.steps} steps")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "batch16_1080p_K200_optimized", "frames": args.frames,
+                   "height": 1080, "width": 1920, "iters": K_ITERS, "order": "optimized",
+                   "l2": "n/a (host)", **PARAMS},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(frames):
+    """The oracle as it stands on the host cores, on about 10-30 s of work:
+    whole frames until 10 s have passed."""
+    import oracle
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    blocks = 0
+    used = 0
+    for img, mask in frames:
+        _, _, gob = oracle.conceal_frame(img, mask, iters=K_ITERS, order=oracle.ORDER_OPTIMIZED,
+                                         threads=threads, **PARAMS)
+        blocks += int((gob >= 0).sum())
+        used += 1
+        if time.perf_counter() - t0 > 10.0:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": blocks / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{used} whole 1920x1080 frame(s) of the workload, {blocks} lost blocks, "
+                      f"OpenMP over the blocks of each group"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2207_00233_gb300 as fse
+
+    frames = make_workload(args.frames)
+    ctx = fse.Context(local)
+    params = fse.make_params(iters=K_ITERS, order=fse.FSE_ORDER_OPTIMIZED,
+                             executor=fse.FSE_EXEC_PERSISTENT, precision=fse.FSE_PREC_FP32,
+                             **PARAMS)
+    tens = []
+    for img, mask in frames:
+        l = torch.from_numpy(img).to(dev)
+        m = torch.from_numpy(mask).to(dev)
+        tens.append((l, m, torch.empty_like(l)))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.fse_conceal_batch(tens, params, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    lost_blocks = ctx.fse_last_batch_info()["lost_blocks"]
+    launches_per_step = ctx.fse_last_batch_info()["launches"]
+
+    # ---- timed region: device time of each step, L2 flushed in between ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kernel_ms = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+            kernel_ms.append(ctx.fse_last_kernel_ms())
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_ms = float(np.sum(step_ms))
+    t_max = t_ms
+    if world > 1:
+        t = torch.tensor([t_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * lost_blocks * args.steps / (t_max / 1e3)
+
+    # ---- end to end through the host-buffer entry point ----
+    pinned = []
+    for img, mask in frames:
+        pinned.append((torch.from_numpy(img).pin_memory(), torch.from_numpy(mask).pin_memory(),
+                       torch.empty(img.shape, dtype=torch.uint8).pin_memory()))
+    host_frames = [(a.numpy(), b.numpy(), c.numpy()) for a, b, c in pinned]
+    for _ in range(2):
+        ctx.fse_conceal_batch_host(host_frames, params, stream)
+    e2e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        ctx.fse_conceal_batch_host(host_frames, params, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    h2d = sum(img.nbytes + mask.nbytes for img, mask in frames)
+    d2h = sum(img.nbytes for img, _ in frames)
+
+    # ---- plain path: one frame per call, one launch per group ----
+    plain = None
+    if not args.no_plain:
+        pp = fse.make_params(iters=K_ITERS, order=fse.FSE_ORDER_OPTIMIZED,
+                             executor=fse.FSE_EXEC_GROUPS, precision=fse.FSE_PREC_FP32, **PARAMS)
+        for t in tens[:2]:
+            ctx.fse_conceal_batch([t], pp, stream)
+        torch.cuda.synchronize()
+        flush.zero_()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for t in tens:
+            ctx.fse_conceal_batch([t], pp, stream)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        plain = lost_blocks / (p0.elapsed_time(p1) / 1e3)
+
+    # ---- roofline of the dominant kernel (the persistent extrapolation) ----
+    k_ms = float(np.mean(kernel_ms))
+    smem_bytes = lost_blocks * K_ITERS * SMEM_BYTES_PER_ITER
+    flops = lost_blocks * K_ITERS * FLOP_PER_ITER
+    clk = clocks.summary()
+    peak_clk_mhz = 2070.0
+    smem_peak = SMS * SMEM_BYTES_PER_CLK * peak_clk_mhz * 1e6 / 1e9  # GB/s
+    fp32_peak = SMS * FP32_LANES * 2 * peak_clk_mhz * 1e6 / 1e12    # TFLOP/s
+    achieved = smem_bytes / (k_ms / 1e3) / 1e9
+    roofline = {"bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
+                "frac": achieved / smem_peak, "traffic": None,
+                "kernel": "k_persistent", "kernel_ms": k_ms,
+                "peak_source": "derived: 152 SMs x 128 B/clk x 2070 MHz (max SM clock)",
+                "fp32": {"achieved_tflops": flops / (k_ms / 1e3) / 1e12, "peak_tflops": fp32_peak,
+                         "frac": flops / (k_ms / 1e3) / 1e12 / fp32_peak}}
+
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(frames)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded generator standing in for the paper's test images)",
+            "config": {"workload": "batch16_1080p_K200_optimized", "frames": args.frames,
+                       "height": 1080, "width": 1920, "iters": K_ITERS, "order": "optimized",
+                       "executor": "persistent", "precision": "fp32",
+                       "lost_blocks_per_step": lost_blocks,
+                       "l2": "flushed between steps (256 MiB write, outside the timed events)",
+                       "parallelism": f"replicas x{world}", **PARAMS},
+            "e2e": {"value": lost_blocks / (e2e_ms / 1e3) * world, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": e2e_ms},
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": roofline,
+            "clocks": clk,
+            "plain_path": None if plain is None else {
+                "value": plain, "unit": UNIT,
+                "what": "same frames, one fse_conceal_batch call per frame, one launch per group"},
+        }
+        if base is not None:
+            line["cpu_baseline"] = base
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,229 @@
+/*
+ * fse.h -- C-ABI of the GB300 (sm_103a) implementation of Frequency Selective
+ * Extrapolation (FSE) block-loss concealment with the line-scan or the
+ * optimized, parallelizable processing order of Seiler & Kaup, "Optimized
+ * and Parallelized Processing Order for Improved Frequency Selective Signal
+ * Extrapolation".
+ *
+ * Every entry point returns an int status (FSE_OK = 0 or an FSE_E* code)
+ * and never aborts the process.  No torch types appear here: buffers are
+ * plain host or device pointers, sizes are ints.
+ *
+ * Method summary (what the library computes for every lost block b):
+ *   1. Extrapolation area L = block b plus a frame of `border` samples
+ *      (Sec. 2, Fig. 1): 48x48 samples for 16x16 blocks and d = 16.
+ *      Sub-areas: A (originally known), R (lost, concealed earlier),
+ *      B_i (lost, inside b), B_o (lost, outside b, still open), and
+ *      samples outside the image.
+ *   2. Weighting, Eq. (2): rho^dist on A, delta * rho^dist on R, 0 on
+ *      B_i, B_o and outside; dist from the area centre ((M-1)/2, (N-1)/2).
+ *   3. Model, Eq. (1): g = sum_k c_k phi_k with 2-D DFT basis functions
+ *      phi_k[m,n] = exp(+j 2 pi (k_m m + k_n n) / 64) (Sec. 4).  Each of K
+ *      iterations selects u = argmax_k |R_w[k]|^2 (largest decrease of the
+ *      weighted residual energy; ties to the smallest k_m * 64 + k_n),
+ *      adds dc = gamma * R_w[u] / W[0] to c_u (orthogonality deficiency
+ *      compensation, gamma = 0.5 in Sec. 4) and updates the weighted
+ *      residual spectrum R_w[k] -= dc * W[(k - u) mod 64] (transform-domain
+ *      form, Sec. 4), where W is the DFT of the weights.
+ *   4. The real part of the model, clamped to [0, 255], is inserted into
+ *      the lost samples of b (Sec. 2); the 8-bit output is rounded half to
+ *      even.  Later blocks read the clamped, unrounded value.
+ *   5. Blocks are processed in line-scan order, or in the groups of
+ *      Algorithm 1 (Sec. 3): all blocks of a group are extrapolated in
+ *      parallel from the frame state at the start of the group.
+ */
+#ifndef FSE_H
+#define FSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define FSE_OK 0
+#define FSE_EINVAL 1     /* bad argument: NULL, size, stride, parameter     */
+#define FSE_ENOMEM 2     /* device/host allocation failed or over budget    */
+#define FSE_EAGAIN 3     /* admission refused for now; retry later          */
+#define FSE_ETIMEDOUT 4  /* a bounded device-side wait gave up              */
+#define FSE_ECUDA 5      /* a CUDA runtime call failed                      */
+#define FSE_ENOTFOUND 6  /* unknown ticket                                  */
+
+/* ---- parameters ---------------------------------------------------------- */
+#define FSE_ORDER_LINESCAN 0   /* conventional raster order, one block at a time */
+#define FSE_ORDER_OPTIMIZED 1  /* Algorithm 1 groups (Sec. 3)                   */
+
+/* Arithmetic of the initial weighted projection (DFT of w*f and of w).  The
+ * iterations always run in FP32.  FSE_PREC_FP32 computes the projection on
+ * the FP32 pipes; the others run it as DFT-as-GEMM on the tensor cores with
+ * FP32 accumulation and the named operand type. */
+#define FSE_PREC_FP32 0
+#define FSE_PREC_TF32 1
+#define FSE_PREC_BF16 2
+#define FSE_PREC_FP16 3
+#define FSE_PREC_BF16X3 4      /* split-BF16 operands (hi*hi + hi*lo + lo*hi) */
+
+/* How the groups are dispatched on the device. */
+#define FSE_EXEC_GROUPS 0      /* one launch per group (plain path)              */
+#define FSE_EXEC_PERSISTENT 1  /* one persistent launch over all frames; a block
+                                  starts once its earlier-group neighbours are
+                                  done (device dependency counters)            */
+
+#define FSE_MAX_ITERS 1024
+
+typedef struct fse_params {
+    int block;      /* block size; 16 is the only supported value          */
+    int border;     /* frame width d around the block; 16 supported        */
+    int dft;        /* DFT size per dimension; 64 supported                */
+    int iters;      /* K, 0 .. FSE_MAX_ITERS (the paper uses 200)          */
+    float rho;      /* weighting decay rho-hat, 0 < rho < 1 (paper: 0.8)   */
+    float delta;    /* weight factor of R, 0 <= delta <= 1 (paper: 0.2)    */
+    float gamma;    /* ODC factor, 0 < gamma <= 1 (paper: 0.5)             */
+    int order;      /* FSE_ORDER_*                                         */
+    int precision;  /* FSE_PREC_*                                          */
+    int executor;   /* FSE_EXEC_*                                          */
+} fse_params;
+
+/* One frame of 8-bit luma.  luma, out and loss_mask are [height][stride]
+ * row-major bytes; loss_mask[y*stride+x] != 0 marks a lost sample.  out may
+ * alias luma.  stride >= width.  A block is lost when any of its in-image
+ * samples is lost. */
+typedef struct fse_frame {
+    const uint8_t *luma;
+    uint8_t *out;
+    const uint8_t *loss_mask;
+    int width, height, stride;
+} fse_frame;
+
+typedef struct fse_ctx fse_ctx;
+
+typedef struct fse_stats {
+    int status;          /* FSE_OK or the error of this request              */
+    int lost_blocks;     /* blocks concealed                                  */
+    int groups;          /* processing-order groups                           */
+    int batch_requests;  /* requests in the device batch that carried it      */
+    double queue_ms;     /* submit -> start of its device batch               */
+    double latency_ms;   /* submit -> result copied back                      */
+} fse_stats;
+
+/* Processing order (Sec. 3, Algorithm 1; or line scan).  Host only.
+ * block_lost: [bh*bw] bytes, non-zero = block has lost samples.
+ * Outputs, caller-owned: group_of_block [bh*bw] (-1 = nothing to do, else
+ * the 0-based group), group_ptr [bh*bw + 1], block_ids [bh*bw] (each group
+ * lists its blocks in raster order; group g is block_ids[group_ptr[g] ..
+ * group_ptr[g+1])), n_groups.  Readings: neighbours are the 8 adjacent
+ * blocks; a corner block gets +5, another margin block +3; N_min is the
+ * minimum over blocks with N >= 0; S is filled in raster order.
+ * Errors: FSE_EINVAL on NULL pointers, bw/bh <= 0 or an unknown order. */
+int fse_plan_order(int bw, int bh, const uint8_t *block_lost, int order,
+                   int32_t *group_of_block, int32_t *group_ptr,
+                   int32_t *block_ids, int32_t *n_groups);
+
+/* Create a context on CUDA device `device`.  mem_budget bounds the device
+ * workspace the context may hold (0 = no limit).  The context owns its
+ * workspace (FP32 working frames, plans, status words) and a serving
+ * thread started on the first fse_submit. */
+int fse_ctx_create(fse_ctx **ctx, int device, size_t mem_budget);
+void fse_ctx_destroy(fse_ctx *ctx);
+
+/* Conceal n frames whose luma/out/loss_mask are DEVICE pointers.
+ * Stream-ordered on `cuda_stream` (a cudaStream_t, NULL = legacy default
+ * stream).  The call plans on the host: it reads the block-loss maps back
+ * and synchronises the stream once before it enqueues the extrapolation;
+ * it returns once the work is enqueued, so buffers must stay valid until
+ * the stream passes it.  Not thread-safe per context.
+ * Errors: FSE_EINVAL (params, sizes, NULL), FSE_ENOMEM, FSE_ECUDA,
+ * FSE_ETIMEDOUT (reported by the next call that synchronises). */
+int fse_conceal_batch(fse_ctx *ctx, const fse_frame *frames, int n,
+                      const fse_params *params, void *cuda_stream);
+
+/* Same as fse_conceal_batch for frames in HOST memory: copies the inputs to
+ * the device, conceals, copies `out` back and synchronises `cuda_stream`
+ * before returning (so it reports FSE_ETIMEDOUT directly). */
+int fse_conceal_batch_host(fse_ctx *ctx, const fse_frame *frames, int n,
+                           const fse_params *params, void *cuda_stream);
+
+/* FSE of n pre-gathered 48x48 areas (DEVICE pointers), for inspection and
+ * parity tests of the per-block computation alone.
+ *   area_f   [n][48][48] float: sample values (ignored where weight is 0)
+ *   area_cls [n][48][48] uint8: 0 = A, 1 = R, 2 = B_i, 3 = B_o, 4 = outside
+ *   g_out    [n][16][16] float: real part of the model on the centre block,
+ *                               unclamped
+ *   u_out    [n][K] int32 (optional): selected index 64*k_m + k_n, -1 if
+ *                               the area has no support
+ *   dc_out   [n][K][2] float (optional): coefficient increments
+ *   r_out    [n][64][64][2] float (optional): weighted residual spectrum
+ *                               after K iterations
+ * Stream-ordered, asynchronous. */
+int fse_extrapolate_areas(fse_ctx *ctx, const float *area_f,
+                          const uint8_t *area_cls, int n,
+                          const fse_params *params, float *g_out,
+                          int32_t *u_out, float *dc_out, float *r_out,
+                          void *cuda_stream);
+
+/* Serving.  fse_submit queues one request whose luma/out/loss_mask are
+ * HOST pointers; they are borrowed until fse_poll reports done.  Requests
+ * are admitted into device batches as workspace memory frees up; batches
+ * overlap on the device (continuous batching).  Non-blocking.
+ * Errors: FSE_EINVAL, FSE_EAGAIN (queue full; retry later). */
+int fse_submit(fse_ctx *ctx, const fse_frame *frame, const fse_params *params,
+               uint64_t *ticket);
+
+/* Non-blocking.  *done = 1 once the request finished (out written); then
+ * *out (optional) receives its statistics and the ticket is released.
+ * Errors: FSE_ENOTFOUND for an unknown or already released ticket. */
+int fse_poll(fse_ctx *ctx, uint64_t ticket, int *done, fse_stats *out);
+
+/* Block until every submitted request has finished (or timeout_ms passes;
+ * returns FSE_ETIMEDOUT then).  timeout_ms < 0 waits without limit. */
+int fse_drain(fse_ctx *ctx, int timeout_ms);
+
+/* Device-side statistics of the last fse_conceal_batch / _host call:
+ * lost blocks, groups (max over frames) and kernel launches enqueued. */
+int fse_last_batch_info(fse_ctx *ctx, int *lost_blocks, int *groups,
+                        int *launches);
+
+/* Device time of the extrapolation launches of the last fse_conceal_batch
+ * or fse_conceal_batch_host call (the persistent kernel, or all group
+ * launches), from CUDA events recorded on the call's stream around them.
+ * Waits for the end event.  *ms = 0 when the batch had nothing to do.
+ * Errors: FSE_EINVAL (NULL), FSE_ECUDA. */
+int fse_last_kernel_ms(fse_ctx *ctx, float *ms);
+
+/* Copy the FP32 working frame of frame `frame` of the last fse_conceal_batch
+ * or fse_conceal_batch_host call into dst (DEVICE pointer, [height][dst_stride]
+ * floats).  Values are defined at lost samples only: the clamped, unrounded
+ * model values that later blocks read; other samples are unspecified.
+ * Valid until the next batch call.  Stream-ordered, asynchronous.
+ * Errors: FSE_EINVAL for a bad index, NULL dst or dst_stride < width. */
+int fse_copy_work(fse_ctx *ctx, int frame, float *dst, int dst_stride,
+                  void *cuda_stream);
+
+/* Context options (host-side settings; take effect on the next batch).
+ *   FSE_OPT_SPIN_LIMIT       polls a device-side dependency wait makes
+ *                            before it gives up with FSE_ETIMEDOUT
+ *                            (default 2^23, about a second)
+ *   FSE_OPT_PERSISTENT_CTAS  CTAs per SM of the persistent launch
+ *                            (0 = as many as fit)
+ *   FSE_OPT_SERVE_SLOTS      concurrent device batches of the server (1..16;
+ *                            before the first fse_submit)
+ *   FSE_OPT_SERVE_MAX_BATCH  requests per device batch (>= 1)
+ *   FSE_OPT_TEST_STUCK_DEP   test hook: 1 adds a dependency that nothing
+ *                            releases to the last work item of the next
+ *                            persistent batch, so its bounded wait runs out
+ * Errors: FSE_EINVAL for an unknown option or value. */
+#define FSE_OPT_SPIN_LIMIT 1
+#define FSE_OPT_PERSISTENT_CTAS 2
+#define FSE_OPT_SERVE_SLOTS 3
+#define FSE_OPT_SERVE_MAX_BATCH 4
+#define FSE_OPT_TEST_STUCK_DEP 5
+int fse_ctx_set_option(fse_ctx *ctx, int option, long long value);
+
+const char *fse_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,690 @@
+// Host runtime of the FSE library: context, device workspace, the batch
+// executors (one launch per processing-order group, or one persistent
+// launch over a dependency graph), and the inspection entry point.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/fse.h"
+#include "fse_ctx.h"
+#include "fse_internal.h"
+
+using namespace fse;
+
+// ---------------------------------------------------------------------------
+// Tables
+// ---------------------------------------------------------------------------
+
+// cos / sin of 2 pi t / 64.  Built from the first octant with the exact
+// symmetries of the circle, so that entries for t and 64 - t are exact
+// mirrors (a real input then has an exactly conjugate-symmetric spectrum)
+// and the axis values are exact.
+static void build_twiddles(float2 *tw) {
+    double c[kDft], s[kDft];
+    const double step = 2.0 * 3.14159265358979323846 / kDft;
+    for (int t = 0; t <= kDft / 8; ++t) {
+        c[t] = std::cos(step * t);
+        s[t] = std::sin(step * t);
+    }
+    for (int t = kDft / 8 + 1; t <= kDft / 4; ++t) {  // reflect about 45 degrees
+        c[t] = s[kDft / 4 - t];
+        s[t] = c[kDft / 4 - t];
+    }
+    c[kDft / 4] = 0.0;
+    s[kDft / 4] = 1.0;
+    for (int t = kDft / 4 + 1; t <= kDft / 2; ++t) {  // second quadrant
+        c[t] = -c[kDft / 2 - t];
+        s[t] = s[kDft / 2 - t];
+    }
+    s[0] = 0.0;
+    s[kDft / 2] = 0.0;
+    for (int t = kDft / 2 + 1; t < kDft; ++t) {  // lower half: conjugates
+        c[t] = c[kDft - t];
+        s[t] = -s[kDft - t];
+    }
+    for (int t = 0; t < kDft; ++t) tw[t] = make_float2((float)c[t], (float)s[t]);
+}
+
+// Eq. (2) distance decay rho^dist over the 48x48 area, centre (23.5, 23.5).
+static void build_rho_table(float rho, float *tab) {
+    const double cm = 0.5 * (kArea - 1);
+    for (int m = 0; m < kArea; ++m)
+        for (int n = 0; n < kArea; ++n) {
+            const double dm = m - cm, dn = n - cm;
+            tab[m * kArea + n] = (float)std::pow((double)rho, std::sqrt(dm * dm + dn * dn));
+        }
+}
+
+// ---------------------------------------------------------------------------
+// Device buffers with budget accounting
+// ---------------------------------------------------------------------------
+
+int fse_ctx::dev_reserve(DevBuf &b, size_t bytes) {
+    if (bytes <= b.cap) return FSE_OK;
+    std::lock_guard<std::mutex> lk(mem_mu);
+    size_t want = std::max(bytes, b.cap + b.cap / 2);
+    want = (want + 255) & ~(size_t)255;
+    if (budget && used + want - b.cap > budget) {
+        want = (bytes + 255) & ~(size_t)255;
+        if (used + want - b.cap > budget) return FSE_ENOMEM;
+    }
+    void *p = nullptr;
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+        cudaGetLastError();
+        return FSE_ENOMEM;
+    }
+    if (b.ptr) {
+        cudaFree(b.ptr);
+        used -= b.cap;
+    }
+    b.ptr = p;
+    b.cap = want;
+    used += want;
+    return FSE_OK;
+}
+
+void fse_ctx::dev_release(DevBuf &b) {
+    std::lock_guard<std::mutex> lk(mem_mu);
+    if (b.ptr) {
+        cudaFree(b.ptr);
+        used -= b.cap;
+    }
+    b.ptr = nullptr;
+    b.cap = 0;
+}
+
+int fse_ctx::host_reserve(HostBuf &b, size_t bytes) {
+    if (bytes <= b.cap) return FSE_OK;
+    size_t want = std::max(bytes, b.cap + b.cap / 2);
+    void *p = nullptr;
+    if (cudaHostAlloc(&p, want, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return FSE_ENOMEM;
+    }
+    if (b.ptr) cudaFreeHost(b.ptr);
+    b.ptr = p;
+    b.cap = want;
+    return FSE_OK;
+}
+
+void fse_ctx::host_release(HostBuf &b) {
+    if (b.ptr) cudaFreeHost(b.ptr);
+    b.ptr = nullptr;
+    b.cap = 0;
+}
+
+const float *fse_ctx::rho_table(float rho, int *rc) {
+    {
+        std::lock_guard<std::mutex> lk(mem_mu);
+        for (auto &e : rho_tabs)
+            if (e.first == rho) return static_cast<const float *>(e.second.ptr);
+    }
+    DevBuf b;
+    *rc = dev_reserve(b, kArea * kArea * sizeof(float));
+    if (*rc) return nullptr;
+    std::vector<float> tab(kArea * kArea);
+    build_rho_table(rho, tab.data());
+    if (cudaMemcpy(b.ptr, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        dev_release(b);
+        *rc = FSE_ECUDA;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(mem_mu);
+    rho_tabs.emplace_back(rho, b);
+    return static_cast<const float *>(b.ptr);
+}
+
+// ---------------------------------------------------------------------------
+// Validation
+// ---------------------------------------------------------------------------
+
+int fse::check_params(const fse_params *p) {
+    if (!p) return FSE_EINVAL;
+    if (p->block != kBlock || p->border != kBorder || p->dft != kDft) return FSE_EINVAL;
+    if (p->iters < 0 || p->iters > FSE_MAX_ITERS) return FSE_EINVAL;
+    if (!(p->rho > 0.f && p->rho < 1.f)) return FSE_EINVAL;
+    if (!(p->delta >= 0.f && p->delta <= 1.f)) return FSE_EINVAL;
+    if (!(p->gamma > 0.f && p->gamma < 2.f)) return FSE_EINVAL;
+    if (p->order != FSE_ORDER_LINESCAN && p->order != FSE_ORDER_OPTIMIZED) return FSE_EINVAL;
+    if (p->executor != FSE_EXEC_GROUPS && p->executor != FSE_EXEC_PERSISTENT) return FSE_EINVAL;
+    if (!precision_supported(p->precision)) return FSE_EINVAL;
+    return FSE_OK;
+}
+
+static int check_frame(const fse_frame &f) {
+    if (!f.luma || !f.out || !f.loss_mask) return FSE_EINVAL;
+    if (f.width <= 0 || f.height <= 0 || f.stride < f.width) return FSE_EINVAL;
+    if ((long long)f.width * f.height > (1LL << 30)) return FSE_EINVAL;
+    return FSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batch execution on device-resident frames
+// ---------------------------------------------------------------------------
+
+#define CK(call)                                   \
+    do {                                           \
+        if ((call) != cudaSuccess) {               \
+            cudaGetLastError();                    \
+            return FSE_ECUDA;                      \
+        }                                          \
+    } while (0)
+
+int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
+                   const fse_params *p, cudaStream_t stream,
+                   const std::vector<std::vector<uint8_t>> *host_lost) {
+    int rc = FSE_OK;
+    const float *rho_tab = ctx->rho_table(p->rho, &rc);
+    if (!rho_tab) return rc;
+    // The staging buffers of the previous batch on this workspace must have
+    // been consumed before they are overwritten.
+    if (ws.staged) {
+        CK(cudaEventSynchronize(ws.staged));
+    }
+
+    // ---- geometry ----
+    std::vector<FrameDesc> fd(n);
+    std::vector<int> lost_off(n + 1, 0);
+    size_t work_floats = 0;
+    int max_rows_x_bw = 0;
+    for (int i = 0; i < n; ++i) {
+        FrameDesc &d = fd[i];
+        d.luma = frames[i].luma;
+        d.mask = frames[i].loss_mask;
+        d.out = frames[i].out;
+        d.H = frames[i].height;
+        d.W = frames[i].width;
+        d.stride = frames[i].stride;
+        d.wstride = (d.W + 31) & ~31;
+        d.bh = (d.H + kBlock - 1) / kBlock;
+        d.bw = (d.W + kBlock - 1) / kBlock;
+        lost_off[i + 1] = lost_off[i] + d.bh * d.bw;
+        work_floats += (size_t)d.H * d.wstride;
+        max_rows_x_bw = std::max(max_rows_x_bw, d.H * d.bw);
+    }
+    const int nblocks = lost_off[n];
+
+    rc = ctx->dev_reserve(ws.frames, sizeof(FrameDesc) * n);
+    if (!rc) rc = ctx->dev_reserve(ws.work, sizeof(float) * work_floats);
+    if (!rc) rc = ctx->dev_reserve(ws.lost, nblocks);
+    if (!rc) rc = ctx->dev_reserve(ws.lost_off, sizeof(int) * (n + 1));
+    if (!rc) rc = ctx->dev_reserve(ws.gob, sizeof(int32_t) * nblocks);
+    if (!rc) rc = ctx->dev_reserve(ws.status, sizeof(int) * 4);
+    if (rc) return rc;
+    {
+        float *wp = static_cast<float *>(ws.work.ptr);
+        for (int i = 0; i < n; ++i) {
+            fd[i].work = wp;
+            fd[i].gob = static_cast<int32_t *>(ws.gob.ptr) + lost_off[i];
+            wp += (size_t)fd[i].H * fd[i].wstride;
+        }
+    }
+
+    // ---- block-loss maps ----
+    std::vector<uint8_t> lost_h(nblocks);
+    int prev_error = 0;
+    if (host_lost) {
+        for (int i = 0; i < n; ++i)
+            std::memcpy(lost_h.data() + lost_off[i], (*host_lost)[i].data(),
+                        (size_t)fd[i].bh * fd[i].bw);
+    } else {
+        rc = ctx->host_reserve(ws.stage, sizeof(FrameDesc) * n + sizeof(int) * (n + 1) +
+                                             nblocks + 64);
+        if (rc) return rc;
+        char *st = static_cast<char *>(ws.stage.ptr);
+        std::memcpy(st, fd.data(), sizeof(FrameDesc) * n);
+        std::memcpy(st + sizeof(FrameDesc) * n, lost_off.data(), sizeof(int) * (n + 1));
+        CK(cudaMemcpyAsync(ws.frames.ptr, st, sizeof(FrameDesc) * n, cudaMemcpyHostToDevice,
+                           stream));
+        CK(cudaMemcpyAsync(ws.lost_off.ptr, st + sizeof(FrameDesc) * n, sizeof(int) * (n + 1),
+                           cudaMemcpyHostToDevice, stream));
+        CK(cudaMemsetAsync(ws.lost.ptr, 0, nblocks, stream));
+        CK(launch_block_loss(static_cast<FrameDesc *>(ws.frames.ptr), n, max_rows_x_bw,
+                             static_cast<uint8_t *>(ws.lost.ptr),
+                             static_cast<int *>(ws.lost_off.ptr), stream));
+        uint8_t *lost_stage = reinterpret_cast<uint8_t *>(st + sizeof(FrameDesc) * n +
+                                                          sizeof(int) * (n + 1));
+        int *err_stage = reinterpret_cast<int *>(
+            (reinterpret_cast<uintptr_t>(lost_stage + nblocks) + 15) & ~(uintptr_t)15);
+        CK(cudaMemcpyAsync(lost_stage, ws.lost.ptr, nblocks, cudaMemcpyDeviceToHost, stream));
+        if (ws.status_live) {
+            CK(cudaMemcpyAsync(err_stage, static_cast<int *>(ws.status.ptr) + 1, sizeof(int),
+                               cudaMemcpyDeviceToHost, stream));
+        }
+        CK(cudaStreamSynchronize(stream));
+        std::memcpy(lost_h.data(), lost_stage, nblocks);
+        if (ws.status_live) prev_error = *err_stage;
+    }
+    if (prev_error) {
+        ws.status_live = false;
+        return FSE_ETIMEDOUT;
+    }
+
+    // ---- processing order per frame (host, integer) ----
+    std::vector<int32_t> gob_h(nblocks), gptr, ids;
+    std::vector<std::vector<int32_t>> frame_gptr(n), frame_ids(n);
+    int max_groups = 0, lost_blocks = 0;
+    for (int i = 0; i < n; ++i) {
+        const int nb = fd[i].bh * fd[i].bw;
+        gptr.assign(nb + 1, 0);
+        ids.assign(nb, 0);
+        int32_t ng = 0;
+        rc = fse_plan_order(fd[i].bw, fd[i].bh, lost_h.data() + lost_off[i], p->order,
+                            gob_h.data() + lost_off[i], gptr.data(), ids.data(), &ng);
+        if (rc) return rc;
+        frame_gptr[i].assign(gptr.begin(), gptr.begin() + ng + 1);
+        frame_ids[i].assign(ids.begin(), ids.begin() + gptr[ng]);
+        max_groups = std::max(max_groups, (int)ng);
+        lost_blocks += gptr[ng];
+    }
+
+    // ---- work items ----
+    std::vector<int2> items;
+    items.reserve(lost_blocks);
+    std::vector<int> group_start(max_groups + 1, 0);
+    for (int g = 0; g < max_groups; ++g) {
+        group_start[g] = (int)items.size();
+        for (int i = 0; i < n; ++i) {
+            const auto &gp = frame_gptr[i];
+            if (g + 1 >= (int)gp.size()) continue;
+            for (int j = gp[g]; j < gp[g + 1]; ++j) items.push_back(make_int2(i, frame_ids[i][j]));
+        }
+    }
+    group_start[max_groups] = (int)items.size();
+
+    // Dependency graph for the persistent executor: for every item, the lost
+    // 8-neighbours of earlier groups (predecessors) and of later groups
+    // (successors).  Items are in group order, so every predecessor of an
+    // item precedes it in the claim order.
+    std::vector<int> deps, succ_ptr, succ;
+    const bool persistent = p->executor == FSE_EXEC_PERSISTENT;
+    if (persistent && lost_blocks > 0) {
+        std::vector<int> item_of(nblocks, -1);
+        for (int k = 0; k < (int)items.size(); ++k)
+            item_of[lost_off[items[k].x] + items[k].y] = k;
+        deps.assign(items.size(), 0);
+        succ_ptr.assign(items.size() + 1, 0);
+        succ.reserve(items.size() * 4);
+        for (int k = 0; k < (int)items.size(); ++k) {
+            const int f = items[k].x, b = items[k].y;
+            const int bw = fd[f].bw, bh = fd[f].bh, by = b / bw, bx = b % bw;
+            const int g = gob_h[lost_off[f] + b];
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if (!(dy | dx)) continue;
+                    const int ny = by + dy, nx = bx + dx;
+                    if (ny < 0 || ny >= bh || nx < 0 || nx >= bw) continue;
+                    const int gn = gob_h[lost_off[f] + ny * bw + nx];
+                    if (gn < 0) continue;
+                    if (gn < g) deps[k] += 1;
+                    else if (gn > g) succ.push_back(item_of[lost_off[f] + ny * bw + nx]);
+                }
+            succ_ptr[k + 1] = (int)succ.size();
+        }
+    }
+
+    // ---- uploads ----
+    const size_t n_items = items.size();
+    rc = ctx->dev_reserve(ws.items, sizeof(int2) * std::max<size_t>(n_items, 1));
+    if (!rc && persistent) {
+        rc = ctx->dev_reserve(ws.deps, sizeof(int) * std::max<size_t>(n_items, 1));
+        if (!rc) rc = ctx->dev_reserve(ws.succ_ptr, sizeof(int) * (n_items + 1));
+        if (!rc) rc = ctx->dev_reserve(ws.succ, sizeof(int) * std::max<size_t>(succ.size(), 1));
+    }
+    if (rc) return rc;
+    if (persistent && ctx->test_stuck_dep && n_items > 0) {
+        deps[n_items - 1] += 1;  // nothing ever releases this dependency
+        ctx->test_stuck_dep = false;
+    }
+    const size_t stage_bytes = sizeof(FrameDesc) * n + sizeof(int32_t) * nblocks +
+                               sizeof(int2) * n_items + sizeof(int) * (2 * n_items + 1) +
+                               sizeof(int) * succ.size() + 256;
+    rc = ctx->host_reserve(ws.stage, stage_bytes);
+    if (rc) return rc;
+    char *st = static_cast<char *>(ws.stage.ptr);
+    size_t off = 0;
+    auto put = [&](void *dev, const void *src, size_t bytes) -> int {
+        if (!bytes) return FSE_OK;
+        std::memcpy(st + off, src, bytes);
+        if (cudaMemcpyAsync(dev, st + off, bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess) {
+            cudaGetLastError();
+            return FSE_ECUDA;
+        }
+        off = (off + bytes + 15) & ~(size_t)15;
+        return FSE_OK;
+    };
+    rc = put(ws.frames.ptr, fd.data(), sizeof(FrameDesc) * n);
+    if (!rc) rc = put(ws.gob.ptr, gob_h.data(), sizeof(int32_t) * nblocks);
+    if (!rc) rc = put(ws.items.ptr, items.data(), sizeof(int2) * n_items);
+    if (!rc && persistent) {
+        rc = put(ws.deps.ptr, deps.data(), sizeof(int) * n_items);
+        if (!rc) rc = put(ws.succ_ptr.ptr, succ_ptr.data(), sizeof(int) * (n_items + 1));
+        if (!rc) rc = put(ws.succ.ptr, succ.data(), sizeof(int) * succ.size());
+    }
+    if (rc) return rc;
+    if (!ws.staged) CK(cudaEventCreateWithFlags(&ws.staged, cudaEventDisableTiming));
+    CK(cudaEventRecord(ws.staged, stream));
+
+    // ---- outputs start as copies of the inputs ----
+    for (int i = 0; i < n; ++i) {
+        if (frames[i].out != frames[i].luma)
+            CK(cudaMemcpy2DAsync(frames[i].out, frames[i].stride, frames[i].luma,
+                                 frames[i].stride, frames[i].width, frames[i].height,
+                                 cudaMemcpyDeviceToDevice, stream));
+    }
+
+    // ---- extrapolation ----
+    const KParams kp{p->rho, p->delta, p->gamma, p->iters};
+    const FrameDesc *fdev = static_cast<const FrameDesc *>(ws.frames.ptr);
+    const float2 *tw_tab = static_cast<const float2 *>(ctx->tw_dev.ptr);
+    int launches = 1;  // block-loss map
+    ws.k_timed = false;
+    if (n_items > 0) {
+        if (!ws.k_begin) {
+            CK(cudaEventCreate(&ws.k_begin));
+            CK(cudaEventCreate(&ws.k_end));
+        }
+        CK(cudaEventRecord(ws.k_begin, stream));
+        if (persistent) {
+            int *status = static_cast<int *>(ws.status.ptr);
+            CK(cudaMemsetAsync(status, 0, sizeof(int) * 2, stream));
+            DepGraph dg;
+            dg.items = static_cast<const int2 *>(ws.items.ptr);
+            dg.deps = static_cast<int *>(ws.deps.ptr);
+            dg.succ_ptr = static_cast<const int *>(ws.succ_ptr.ptr);
+            dg.succ = static_cast<const int *>(ws.succ.ptr);
+            dg.head = status;
+            dg.error = status + 1;
+            dg.n = (int)n_items;
+            dg.spin_limit = ctx->spin_limit;
+            int per_sm = max_resident_ctas(p->iters);
+            if (ctx->persistent_ctas > 0) per_sm = std::min(per_sm, ctx->persistent_ctas);
+            const int grid = std::min<int>((int)n_items, ctx->num_sms * per_sm);
+            CK(launch_persistent(fdev, dg, kp, rho_tab, tw_tab, p->precision, grid, stream));
+            ws.status_live = true;
+            launches += 1;
+        } else {
+            const int2 *idev = static_cast<const int2 *>(ws.items.ptr);
+            for (int g = 0; g < max_groups; ++g) {
+                const int cnt = group_start[g + 1] - group_start[g];
+                CK(launch_group(fdev, idev + group_start[g], cnt, kp, rho_tab, tw_tab,
+                                p->precision, stream));
+                launches += 1;
+            }
+        }
+        CK(cudaEventRecord(ws.k_end, stream));
+        ws.k_timed = true;
+    }
+    ws.lost_blocks = lost_blocks;
+    ws.groups = max_groups;
+    ws.launches = launches;
+    ws.work_ptr.resize(n);
+    ws.work_w.resize(n);
+    ws.work_h.resize(n);
+    ws.work_stride.resize(n);
+    for (int i = 0; i < n; ++i) {
+        ws.work_ptr[i] = fd[i].work;
+        ws.work_w[i] = fd[i].W;
+        ws.work_h[i] = fd[i].H;
+        ws.work_stride[i] = fd[i].wstride;
+    }
+    return FSE_OK;
+}
+
+// Reads the status word of the last persistent launch (after a sync).
+int fse::read_status(fse_ctx *, Workspace &ws, cudaStream_t stream) {
+    if (!ws.status_live) return FSE_OK;
+    int err = 0;
+    if (cudaMemcpyAsync(&err, static_cast<int *>(ws.status.ptr) + 1, sizeof(int),
+                        cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess) {
+        cudaGetLastError();
+        return FSE_ECUDA;
+    }
+    ws.status_live = false;
+    return err ? FSE_ETIMEDOUT : FSE_OK;
+}
+
+void fse::release_workspace(fse_ctx *ctx, Workspace &ws) {
+    ctx->dev_release(ws.frames);
+    ctx->dev_release(ws.work);
+    ctx->dev_release(ws.lost);
+    ctx->dev_release(ws.lost_off);
+    ctx->dev_release(ws.gob);
+    ctx->dev_release(ws.items);
+    ctx->dev_release(ws.deps);
+    ctx->dev_release(ws.succ_ptr);
+    ctx->dev_release(ws.succ);
+    ctx->dev_release(ws.status);
+    ctx->dev_release(ws.d_luma);
+    ctx->dev_release(ws.d_mask);
+    ctx->dev_release(ws.d_out);
+    ctx->host_release(ws.stage);
+    if (ws.staged) cudaEventDestroy(ws.staged);
+    if (ws.k_begin) cudaEventDestroy(ws.k_begin);
+    if (ws.k_end) cudaEventDestroy(ws.k_end);
+    ws.staged = ws.k_begin = ws.k_end = nullptr;
+    ws.k_timed = false;
+}
+
+// ---------------------------------------------------------------------------
+// C-ABI
+// ---------------------------------------------------------------------------
+
+extern "C" int fse_ctx_create(fse_ctx **out, int device, size_t mem_budget) {
+    if (!out) return FSE_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return FSE_ECUDA;
+    }
+    if (device < 0 || device >= ndev) return FSE_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return FSE_ECUDA;
+    }
+    fse_ctx *c = new (std::nothrow) fse_ctx();
+    if (!c) return FSE_ENOMEM;
+    c->device = device;
+    c->budget = mem_budget;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return FSE_ECUDA;
+    }
+    c->num_sms = prop.multiProcessorCount;
+    float2 tw[kDft];
+    build_twiddles(tw);
+    int rc = c->dev_reserve(c->tw_dev, sizeof(tw));
+    if (rc || cudaMemcpy(c->tw_dev.ptr, tw, sizeof(tw), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        c->dev_release(c->tw_dev);
+        delete c;
+        return rc ? rc : FSE_ECUDA;
+    }
+    *out = c;
+    return FSE_OK;
+}
+
+extern "C" void fse_ctx_destroy(fse_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    stop_server(ctx);
+    cudaDeviceSynchronize();
+    release_workspace(ctx, ctx->ws);
+    ctx->dev_release(ctx->tw_dev);
+    for (auto &e : ctx->rho_tabs) ctx->dev_release(e.second);
+    delete ctx;
+}
+
+extern "C" int fse_conceal_batch(fse_ctx *ctx, const fse_frame *frames, int n,
+                                 const fse_params *params, void *cuda_stream) {
+    if (!ctx || !frames || n <= 0) return FSE_EINVAL;
+    int rc = check_params(params);
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i)
+        if ((rc = check_frame(frames[i]))) return rc;
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    cudaSetDevice(ctx->device);
+    rc = run_batch(ctx, ctx->ws, frames, n, params, static_cast<cudaStream_t>(cuda_stream),
+                   nullptr);
+    ctx->last_lost_blocks = ctx->ws.lost_blocks;
+    ctx->last_groups = ctx->ws.groups;
+    ctx->last_launches = ctx->ws.launches;
+    return rc;
+}
+
+extern "C" int fse_conceal_batch_host(fse_ctx *ctx, const fse_frame *frames, int n,
+                                      const fse_params *params, void *cuda_stream) {
+    if (!ctx || !frames || n <= 0) return FSE_EINVAL;
+    int rc = check_params(params);
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i)
+        if ((rc = check_frame(frames[i]))) return rc;
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    cudaSetDevice(ctx->device);
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    Workspace &ws = ctx->ws;
+    size_t total = 0;
+    std::vector<size_t> off(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        off[i + 1] = off[i] + (((size_t)frames[i].height * frames[i].width + 255) & ~(size_t)255);
+    }
+    total = off[n];
+    rc = ctx->dev_reserve(ws.d_luma, total);
+    if (!rc) rc = ctx->dev_reserve(ws.d_mask, total);
+    if (!rc) rc = ctx->dev_reserve(ws.d_out, total);
+    if (rc) return rc;
+    std::vector<fse_frame> dev(n);
+    for (int i = 0; i < n; ++i) {
+        const fse_frame &h = frames[i];
+        uint8_t *dl = static_cast<uint8_t *>(ws.d_luma.ptr) + off[i];
+        uint8_t *dm = static_cast<uint8_t *>(ws.d_mask.ptr) + off[i];
+        uint8_t *dout = static_cast<uint8_t *>(ws.d_out.ptr) + off[i];
+        CK(cudaMemcpy2DAsync(dl, h.width, h.luma, h.stride, h.width, h.height,
+                             cudaMemcpyHostToDevice, stream));
+        CK(cudaMemcpy2DAsync(dm, h.width, h.loss_mask, h.stride, h.width, h.height,
+                             cudaMemcpyHostToDevice, stream));
+        dev[i] = fse_frame{dl, dout, dm, h.width, h.height, h.width};
+    }
+    rc = run_batch(ctx, ws, dev.data(), n, params, stream, nullptr);
+    ctx->last_lost_blocks = ws.lost_blocks;
+    ctx->last_groups = ws.groups;
+    ctx->last_launches = ws.launches;
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i) {
+        const fse_frame &h = frames[i];
+        CK(cudaMemcpy2DAsync(h.out, h.stride, dev[i].out, h.width, h.width, h.height,
+                             cudaMemcpyDeviceToHost, stream));
+    }
+    CK(cudaStreamSynchronize(stream));
+    return read_status(ctx, ws, stream);
+}
+
+extern "C" int fse_extrapolate_areas(fse_ctx *ctx, const float *area_f,
+                                     const uint8_t *area_cls, int n, const fse_params *params,
+                                     float *g_out, int32_t *u_out, float *dc_out, float *r_out,
+                                     void *cuda_stream) {
+    if (!ctx || !area_f || !area_cls || !g_out || n < 0) return FSE_EINVAL;
+    int rc = check_params(params);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    cudaSetDevice(ctx->device);
+    const float *rho_tab = ctx->rho_table(params->rho, &rc);
+    if (!rho_tab) return rc;
+    const KParams kp{params->rho, params->delta, params->gamma, params->iters};
+    CK(launch_areas(area_f, area_cls, n, kp, rho_tab,
+                    static_cast<const float2 *>(ctx->tw_dev.ptr), params->precision, g_out,
+                    u_out, dc_out, r_out, static_cast<cudaStream_t>(cuda_stream)));
+    return FSE_OK;
+}
+
+extern "C" int fse_last_batch_info(fse_ctx *ctx, int *lost_blocks, int *groups, int *launches) {
+    if (!ctx) return FSE_EINVAL;
+    if (lost_blocks) *lost_blocks = ctx->last_lost_blocks;
+    if (groups) *groups = ctx->last_groups;
+    if (launches) *launches = ctx->last_launches;
+    return FSE_OK;
+}
+
+extern "C" int fse_last_kernel_ms(fse_ctx *ctx, float *ms) {
+    if (!ctx || !ms) return FSE_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    *ms = 0.f;
+    if (!ctx->ws.k_timed) return FSE_OK;
+    cudaSetDevice(ctx->device);
+    CK(cudaEventSynchronize(ctx->ws.k_end));
+    CK(cudaEventElapsedTime(ms, ctx->ws.k_begin, ctx->ws.k_end));
+    return FSE_OK;
+}
+
+extern "C" int fse_copy_work(fse_ctx *ctx, int frame, float *dst, int dst_stride,
+                             void *cuda_stream) {
+    if (!ctx || !dst) return FSE_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    const Workspace &ws = ctx->ws;
+    if (frame < 0 || frame >= (int)ws.work_ptr.size()) return FSE_EINVAL;
+    if (dst_stride < ws.work_w[frame]) return FSE_EINVAL;
+    cudaSetDevice(ctx->device);
+    CK(cudaMemcpy2DAsync(dst, sizeof(float) * dst_stride, ws.work_ptr[frame],
+                         sizeof(float) * ws.work_stride[frame], sizeof(float) * ws.work_w[frame],
+                         ws.work_h[frame], cudaMemcpyDeviceToDevice,
+                         static_cast<cudaStream_t>(cuda_stream)));
+    return FSE_OK;
+}
+
+extern "C" int fse_ctx_set_option(fse_ctx *ctx, int option, long long value) {
+    if (!ctx) return FSE_EINVAL;
+    switch (option) {
+    case FSE_OPT_SPIN_LIMIT:
+        if (value < 1) return FSE_EINVAL;
+        ctx->spin_limit = value;
+        return FSE_OK;
+    case FSE_OPT_PERSISTENT_CTAS:
+        if (value < 0 || value > 32) return FSE_EINVAL;
+        ctx->persistent_ctas = (int)value;
+        return FSE_OK;
+    case FSE_OPT_SERVE_SLOTS: {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (value < 1 || value > 16 || ctx->server_started) return FSE_EINVAL;
+        ctx->n_slots = (int)value;
+        return FSE_OK;
+    }
+    case FSE_OPT_SERVE_MAX_BATCH: {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (value < 1 || value > 4096) return FSE_EINVAL;
+        ctx->max_batch = (int)value;
+        return FSE_OK;
+    }
+    case FSE_OPT_TEST_STUCK_DEP:
+        if (value != 0 && value != 1) return FSE_EINVAL;
+        ctx->test_stuck_dep = value != 0;
+        return FSE_OK;
+    default:
+        return FSE_EINVAL;
+    }
+}
+
+extern "C" const char *fse_strerror(int status) {
+    switch (status) {
+    case FSE_OK: return "ok";
+    case FSE_EINVAL: return "invalid argument";
+    case FSE_ENOMEM: return "out of memory or over the context's memory budget";
+    case FSE_EAGAIN: return "admission refused; retry later";
+    case FSE_ETIMEDOUT: return "a bounded device wait timed out";
+    case FSE_ECUDA: return "CUDA runtime error";
+    case FSE_ENOTFOUND: return "unknown ticket";
+    default: return "unknown status";
+    }
+}

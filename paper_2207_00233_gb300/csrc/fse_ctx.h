@@ -1,0 +1,114 @@
+// Context, workspace and serving state of the FSE library (host side).
+#pragma once
+
+#include <chrono>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/fse.h"
+
+namespace fse {
+
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t cap = 0;
+};
+struct HostBuf {
+    void *ptr = nullptr;
+    size_t cap = 0;
+};
+
+// Everything one in-flight batch needs on the device.
+struct Workspace {
+    DevBuf frames, work, lost, lost_off, gob, items, deps, succ_ptr, succ, status;
+    DevBuf d_luma, d_mask, d_out;  // device copies of host frames
+    HostBuf stage;                 // pinned staging for uploads / readback
+    HostBuf io;                    // pinned staging of serving frames
+    cudaEvent_t staged = nullptr;  // uploads from `stage` are complete
+    cudaEvent_t k_begin = nullptr, k_end = nullptr;  // around the extrapolation
+    bool k_timed = false;
+    bool status_live = false;      // status word of a persistent launch pending
+    int lost_blocks = 0, groups = 0, launches = 0;  // of the last batch
+    std::vector<float *> work_ptr;                  // per frame of the last batch
+    std::vector<int> work_w, work_h, work_stride;
+};
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t ticket = 0;
+    fse_frame frame{};
+    fse_params params{};
+    Clock::time_point t_submit, t_start;
+    fse_stats stats{};
+    bool done = false;
+    size_t io_off = 0;
+};
+
+struct Slot {
+    Workspace ws;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done_ev = nullptr;
+    std::vector<Request *> reqs;
+    bool busy = false;
+};
+
+int check_params(const fse_params *p);
+
+}  // namespace fse
+
+struct fse_ctx {
+    int device = 0;
+    size_t budget = 0;  // 0 = unlimited
+    size_t used = 0;    // bytes of device memory held
+    int num_sms = 1;
+    long long spin_limit = 1LL << 23;
+    int persistent_ctas = 0;   // per SM; 0 = occupancy limit
+    bool test_stuck_dep = false;
+
+    fse::DevBuf tw_dev;                                   // 64 twiddles
+    std::vector<std::pair<float, fse::DevBuf>> rho_tabs;  // Eq. (2) decay per rho
+    fse::Workspace ws;  // synchronous API
+    std::mutex api_mu;  // one synchronous API call at a time
+    std::mutex mem_mu;  // budget accounting and table cache
+
+    int last_lost_blocks = 0, last_groups = 0, last_launches = 0;
+
+    // serving
+    std::mutex mu;  // guards everything below and the budget accounting
+    std::condition_variable cv, done_cv;
+    std::thread server;
+    bool server_started = false, stop = false;
+    std::deque<fse::Request *> pending;
+    std::unordered_map<uint64_t, fse::Request *> tickets;
+    uint64_t next_ticket = 1;
+    size_t max_pending = 1 << 16;
+    int n_slots = 4;
+    int max_batch = 32;
+    std::vector<fse::Slot> slots;
+    int outstanding = 0;
+
+    int dev_reserve(fse::DevBuf &b, size_t bytes);
+    void dev_release(fse::DevBuf &b);
+    int host_reserve(fse::HostBuf &b, size_t bytes);
+    void host_release(fse::HostBuf &b);
+    // Device table of rho^dist for this rho (created once, kept until
+    // destroy); nullptr on failure.
+    const float *rho_table(float rho, int *rc);
+};
+
+namespace fse {
+int run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
+              const fse_params *p, cudaStream_t stream,
+              const std::vector<std::vector<uint8_t>> *host_lost);
+int read_status(fse_ctx *ctx, Workspace &ws, cudaStream_t stream);
+void release_workspace(fse_ctx *ctx, Workspace &ws);
+void stop_server(fse_ctx *ctx);
+}  // namespace fse

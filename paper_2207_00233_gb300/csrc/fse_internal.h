@@ -1,0 +1,99 @@
+// Internal declarations shared by the library's translation units
+// (device kernels in fse_kernels.cu, host runtime in fse_api.cpp).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace fse {
+
+// Fixed geometry of the supported configuration: 16x16 blocks, a 16-sample
+// frame around the block (Sec. 4: d = 16), a 48x48 extrapolation area and a
+// 64x64 DFT basis.
+constexpr int kBlock = 16;
+constexpr int kBorder = 16;
+constexpr int kArea = kBlock + 2 * kBorder;  // 48
+constexpr int kDft = 64;
+constexpr int kThreads = 256;                // one CTA per lost block
+constexpr int kWarps = kThreads / 32;
+
+// Shared-memory layout of the per-block CTA (bytes).  The weight spectrum W
+// is stored as W4[row][j] = (Re W[row][j], Re W[row][j^32], Im W[row][j],
+// Im W[row][j^32]) so that one 16-byte load gives a thread both columns it
+// owns; rows 0..6 are repeated as rows 64..70 so that the eight consecutive
+// rows a thread reads never wrap.  Before the iterations the same region
+// holds the area tiles and the first projection stage.
+constexpr int kW4Rows = kDft + 7;
+constexpr int kW4Bytes = kW4Rows * kDft * 16;          // 72704
+constexpr int kTwOff = kW4Bytes;                       // 64 x float2
+constexpr int kRedOff = kTwOff + kDft * 8;             // reduction scratch
+constexpr int kRedBytes = 8 * 4 + 8 * 16 + 64;         // smax[8], cand[8], misc
+constexpr int kListOff = kRedOff + kRedBytes;          // dc list, then u list
+inline int smem_bytes(int iters) {
+    return kListOff + iters * 8 + ((iters * 2 + 15) / 16) * 16;
+}
+
+// Scratch inside the W4 region before the iterations.
+constexpr int kXTileOff = 0;                                // 48x48 float: w*f
+constexpr int kWTileOff = kXTileOff + kArea * kArea * 4;    // 48x48 float: w
+constexpr int kHalfCols = kDft / 2 + 1;                     // 33 (real input)
+constexpr int kYxOff = kWTileOff + kArea * kArea * 4;       // 48x33 float2
+constexpr int kYwOff = kYxOff + kArea * kHalfCols * 8;      // 48x33 float2
+static_assert(kYwOff + kArea * kHalfCols * 8 <= kW4Bytes, "scratch overflow");
+
+struct KParams {
+    float rho, delta, gamma;
+    int iters;
+};
+
+// Device-side description of one frame of a batch.
+struct FrameDesc {
+    const uint8_t *luma;     // [H][stride]
+    const uint8_t *mask;     // [H][stride], non-zero = lost
+    uint8_t *out;            // [H][stride]
+    float *work;             // [H][wstride] FP32 working frame
+    const int32_t *gob;      // [bh][bw] group of each block, -1 = no loss
+    int H, W, stride, wstride, bh, bw;
+    int pad0, pad1;
+};
+
+// Dependency graph of the persistent executor: items are (frame, block)
+// pairs sorted by group; deps[i] counts the lost 8-neighbours of item i
+// from earlier groups still to finish; succ lists the later-group lost
+// 8-neighbours of every item (CSR).
+struct DepGraph {
+    const int2 *items;       // [n] (frame, block)
+    int *deps;               // [n]
+    const int *succ_ptr;     // [n+1]
+    const int *succ;         // [succ_ptr[n]]
+    int *head;               // work counter
+    int *error;              // status word: 0 ok, else FSE_ETIMEDOUT
+    int n;
+    long long spin_limit;    // polls before a wait gives up
+};
+
+// Launchers (fse_kernels.cu).  All are asynchronous on `stream`.
+cudaError_t launch_block_loss(const FrameDesc *frames_dev, int n_frames,
+                              int max_blocks, uint8_t *lost_out,
+                              const int *lost_off_dev, cudaStream_t stream);
+cudaError_t launch_init_frames(const FrameDesc *frames_dev, int n_frames,
+                               int max_pixels, cudaStream_t stream);
+cudaError_t launch_group(const FrameDesc *frames_dev, const int2 *items,
+                         int n_items, const KParams &kp, const float *rho_tab,
+                         const float2 *tw_tab, int precision,
+                         cudaStream_t stream);
+cudaError_t launch_persistent(const FrameDesc *frames_dev, const DepGraph &dg,
+                              const KParams &kp, const float *rho_tab,
+                              const float2 *tw_tab, int precision, int grid,
+                              cudaStream_t stream);
+cudaError_t launch_areas(const float *area_f, const uint8_t *area_cls, int n,
+                         const KParams &kp, const float *rho_tab,
+                         const float2 *tw_tab, int precision, float *g_out,
+                         int32_t *u_out, float *dc_out, float *r_out,
+                         cudaStream_t stream);
+int max_resident_ctas(int iters);   // CTAs of the block kernel per SM
+bool precision_supported(int precision);
+
+}  // namespace fse

@@ -1,0 +1,564 @@
+// sm_103a kernels of Frequency Selective Extrapolation (FSE) block
+// concealment (Seiler & Kaup, Sec. 2 and Sec. 4) and the dispatch of the
+// processing-order groups (Sec. 3, Algorithm 1).
+//
+// One CTA of 256 threads extrapolates one lost 16x16 block:
+//   gather   48x48 area from the frame, sub-area classes, Eq. (2) weights
+//   project  R_w = DFT64(w*f), W = DFT64(w)  (separable; real input)
+//   iterate  K x { u = argmax |R_w|^2 ; dc = gamma R_w[u] / W[0] ;
+//                  R_w[k] -= dc W[k - u] }       (Sec. 4, transform domain)
+//   insert   Re sum dc_i phi_{u_i} on the lost samples of the block (Eq. (1))
+//
+// Thread (warp w, lane l) owns the 16 spectrum entries k_m = 8w + r
+// (r = 0..7), k_n in {l, l + 32}; each (r) pair is held as two packed
+// f32x2 registers (real parts, imaginary parts) so the update runs on the
+// paired FP32 instructions of sm_100-class SMs.  W lives in shared memory
+// in the W4 layout (see fse_internal.h): one 16-byte load per pair.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/fse.h"
+#include "fse_internal.h"
+
+namespace fse {
+namespace {
+
+typedef unsigned long long u64;
+
+// ---- packed FP32 pairs ------------------------------------------------------
+__device__ __forceinline__ u64 pack2(float lo, float hi) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 unpack2(u64 v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// |R|^2 of a pair; the same instruction sequence is used wherever an
+// energy is compared, so equal inputs give bit-identical energies.
+__device__ __forceinline__ u64 energy2(u64 re, u64 im) {
+    return fma2(im, im, mul2(re, re));
+}
+__device__ __forceinline__ void lds_pair(uint32_t addr, u64 &a, u64 &b) {
+    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
+}
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// ---- sources: where an area comes from and where its result goes -----------
+
+// A block of a frame in a batch.  Classes follow Sec. 2: a lost sample of a
+// block from an earlier group is R, of the block itself B_i, of a later
+// group B_o.
+struct FrameSrc {
+    const FrameDesc &fd;
+    int by, bx, self, gself;
+
+    __device__ FrameSrc(const FrameDesc &f, int block)
+        : fd(f), by(block / f.bw), bx(block % f.bw), self(block), gself(f.gob[block]) {}
+
+    __device__ void gather(float *xt, float *wt, const float *rho_tab, float delta) const {
+        const int y0 = by * kBlock - kBorder, x0 = bx * kBlock - kBorder;
+        for (int p = threadIdx.x; p < kArea * kArea; p += kThreads) {
+            const int m = p / kArea, n = p - m * kArea;
+            const int y = y0 + m, x = x0 + n;
+            float w = 0.f, v = 0.f;
+            if (y >= 0 && y < fd.H && x >= 0 && x < fd.W) {
+                const size_t q = (size_t)y * fd.stride + x;
+                if (!fd.mask[q]) {
+                    w = rho_tab[p];
+                    v = (float)fd.luma[q];
+                } else {
+                    const int cb = (y / kBlock) * fd.bw + (x / kBlock);
+                    if (cb != self) {
+                        const int gc = fd.gob[cb];
+                        if (gc >= 0 && gc < gself) {
+                            w = delta * rho_tab[p];
+                            v = __ldcg(fd.work + (size_t)y * fd.wstride + x);
+                        }
+                    }
+                }
+            }
+            xt[p] = w * v;
+            wt[p] = w;
+        }
+    }
+
+    // Thread t holds the model value of sample (t / 16, t % 16) of the block.
+    __device__ void store(float g) const {
+        const int i = threadIdx.x >> 4, j = threadIdx.x & 15;
+        const int y = by * kBlock + i, x = bx * kBlock + j;
+        if (y >= fd.H || x >= fd.W) return;
+        const size_t q = (size_t)y * fd.stride + x;
+        if (!fd.mask[q]) return;
+        const float v = fminf(fmaxf(g, 0.f), 255.f);
+        fd.work[(size_t)y * fd.wstride + x] = v;
+        fd.out[q] = (uint8_t)__float2int_rn(v);
+    }
+};
+
+// A pre-gathered area with explicit classes (inspection entry point).
+struct AreaSrc {
+    const float *f;
+    const uint8_t *cls;
+    float *g;
+
+    __device__ void gather(float *xt, float *wt, const float *rho_tab, float delta) const {
+        for (int p = threadIdx.x; p < kArea * kArea; p += kThreads) {
+            const int c = cls[p];
+            float w = 0.f;
+            if (c == 0) w = rho_tab[p];
+            else if (c == 1) w = delta * rho_tab[p];
+            xt[p] = (w != 0.f) ? w * f[p] : 0.f;
+            wt[p] = w;
+        }
+    }
+    __device__ void store(float gv) const { g[threadIdx.x] = gv; }
+};
+
+struct Trace {
+    int32_t *u;   // [K] or null
+    float *dc;    // [K][2] or null
+    float *r;     // [64][64][2] or null
+};
+
+// Stage 2 of the projection for the entries of thread (w, l):
+// X[k_m][k_n] = sum_m exp(-j 2 pi k_m m / 64) Y[m][k_n] for k_m = 8w + r and
+// k_n in {l, l + 32}; column l + 32 comes from the conjugate of 32 - l.
+__device__ __forceinline__ void stage2_rows(const float2 *y, const float2 *tw, int w, int l,
+                                            float (&ar)[8][2], float (&ai)[8][2]) {
+    for (int m = 0; m < kArea; ++m) {
+        const float2 a = y[m * kHalfCols + l];
+        float2 b = y[m * kHalfCols + 32 - l];
+        b.y = -b.y;
+        const int t0 = (8 * w * m) & (kDft - 1);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const float2 cs = tw[(t0 + r * m) & (kDft - 1)];
+            // (c - j s) (y_r + j y_i) = (c y_r + s y_i) + j (c y_i - s y_r)
+            ar[r][0] = fmaf(cs.x, a.x, fmaf(cs.y, a.y, ar[r][0]));
+            ai[r][0] = fmaf(cs.x, a.y, fmaf(-cs.y, a.x, ai[r][0]));
+            ar[r][1] = fmaf(cs.x, b.x, fmaf(cs.y, b.y, ar[r][1]));
+            ai[r][1] = fmaf(cs.x, b.y, fmaf(-cs.y, b.x, ai[r][1]));
+        }
+    }
+}
+
+// ---- projection on the FP32 pipes --------------------------------------------
+// Stage 1 (along n) for both inputs, using the conjugate symmetry of a real
+// input's spectrum: Y[m][k_n] for k_n = 0..32.  Stage 2 (along m) produces
+// the entries each thread owns: R_w into registers, W into temporaries.
+__device__ __forceinline__ void project_fp32(unsigned char *smem, const float2 *tw,
+                                             u64 (&rre)[8], u64 (&rim)[8],
+                                             float (&wre)[8][2], float (&wim)[8][2]) {
+    const float *xt = reinterpret_cast<const float *>(smem + kXTileOff);
+    const float *wt = reinterpret_cast<const float *>(smem + kWTileOff);
+    float2 *yx = reinterpret_cast<float2 *>(smem + kYxOff);
+    float2 *yw = reinterpret_cast<float2 *>(smem + kYwOff);
+    const int tid = threadIdx.x;
+
+    constexpr int kOut = kArea * kHalfCols;  // 1584 per input
+    for (int o = tid; o < 2 * kOut; o += kThreads) {
+        const int which = o >= kOut;
+        const int rem = o - which * kOut;
+        const int m = rem / kHalfCols, kn = rem - m * kHalfCols;
+        const float *row = (which ? wt : xt) + m * kArea;
+        float re = 0.f, im = 0.f;
+        int t = 0;
+#pragma unroll 8
+        for (int n = 0; n < kArea; ++n) {
+            const float v = row[n];
+            const float2 cs = tw[t];
+            re = fmaf(v, cs.x, re);
+            im = fmaf(-v, cs.y, im);
+            t = (t + kn) & (kDft - 1);
+        }
+        (which ? yw : yx)[m * kHalfCols + kn] = make_float2(re, im);
+    }
+    __syncthreads();
+
+    const int w = tid >> 5, l = tid & 31;
+    // x pass, then w pass: only one set of accumulators grows at a time.
+    {
+        float ar[8][2], ai[8][2];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) ar[r][0] = ar[r][1] = ai[r][0] = ai[r][1] = 0.f;
+        stage2_rows(yx, tw, w, l, ar, ai);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            rre[r] = pack2(ar[r][0], ar[r][1]);
+            rim[r] = pack2(ai[r][0], ai[r][1]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) wre[r][0] = wre[r][1] = wim[r][0] = wim[r][1] = 0.f;
+    stage2_rows(yw, tw, w, l, wre, wim);
+}
+
+// Store the thread's W entries in the W4 layout (plus the repeated rows).
+__device__ __forceinline__ void store_w4(unsigned char *smem, const float (&wre)[8][2],
+                                         const float (&wim)[8][2]) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    float4 *w4 = reinterpret_cast<float4 *>(smem);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int row = 8 * w + r;
+        const float4 a = make_float4(wre[r][0], wre[r][1], wim[r][0], wim[r][1]);
+        const float4 b = make_float4(wre[r][1], wre[r][0], wim[r][1], wim[r][0]);
+        w4[row * kDft + l] = a;
+        w4[row * kDft + l + 32] = b;
+        if (row < kW4Rows - kDft) {
+            w4[(row + kDft) * kDft + l] = a;
+            w4[(row + kDft) * kDft + l + 32] = b;
+        }
+    }
+}
+
+// One pass over the thread's entries: R -= dc * W[k - u] (dc = 0 leaves R
+// bit-identical) and the thread's largest |R|^2.
+__device__ __forceinline__ float update_and_max(uint32_t wbase, u64 ndcr2, u64 dci2,
+                                                u64 ndci2, u64 (&rre)[8], u64 (&rim)[8]) {
+    float mx = 0.f;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        u64 wr, wi;
+        lds_pair(wbase + r * (kDft * 16), wr, wi);
+        u64 a = fma2(wr, ndcr2, rre[r]);
+        a = fma2(wi, dci2, a);
+        u64 b = fma2(wi, ndcr2, rim[r]);
+        b = fma2(wr, ndci2, b);
+        rre[r] = a;
+        rim[r] = b;
+        const float2 e = unpack2(energy2(a, b));
+        mx = fmaxf(mx, fmaxf(e.x, e.y));
+    }
+    return mx;
+}
+
+__device__ __forceinline__ uint32_t w4_base(uint32_t w4addr, int um, int un) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int row = (8 * w - um) & (kDft - 1);
+    const int col = (l - un) & (kDft - 1);
+    return w4addr + (uint32_t)(row * kDft + col) * 16u;
+}
+
+// The full per-block computation.  Returns the model value of this thread's
+// sample of the centre block (unclamped).
+template <bool kTrace, class Src>
+__device__ __forceinline__ float run_block(const Src &src, const KParams &kp,
+                                           const float *rho_tab, const float2 *tw_g,
+                                           unsigned char *smem, const Trace &tr) {
+    const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+    float2 *tw = reinterpret_cast<float2 *>(smem + kTwOff);
+    uint32_t *smax = reinterpret_cast<uint32_t *>(smem + kRedOff);
+    float4 *cand = reinterpret_cast<float4 *>(smem + kRedOff + 32);
+    float *misc = reinterpret_cast<float *>(smem + kRedOff + 32 + 128);
+    float2 *dcl = reinterpret_cast<float2 *>(smem + kListOff);
+    uint16_t *ul = reinterpret_cast<uint16_t *>(smem + kListOff + kp.iters * 8);
+
+    if (tid < kDft) tw[tid] = tw_g[tid];
+    src.gather(reinterpret_cast<float *>(smem + kXTileOff),
+               reinterpret_cast<float *>(smem + kWTileOff), rho_tab, kp.delta);
+    __syncthreads();
+
+    u64 rre[8], rim[8];
+    {
+        float wre[8][2], wim[8][2];
+        project_fp32(smem, tw, rre, rim, wre, wim);
+        __syncthreads();  // all reads of the stage-1 scratch are done
+        store_w4(smem, wre, wim);
+        if (tid == 0) misc[0] = wre[0][0];  // W[0] = sum of the weights
+    }
+    __syncthreads();
+
+    const float W0 = misc[0];
+    const int K = (W0 > 0.f) ? kp.iters : 0;
+    const float gw = kp.gamma / fmaxf(W0, 1e-30f);
+    const uint32_t w4addr = smem_addr(smem);
+
+    u64 ndcr2 = 0ull, dci2 = 0ull, ndci2 = 0ull;  // first pass: dc = 0
+    uint32_t wbase = w4_base(w4addr, 0, 0);
+    for (int it = 0; it < K; ++it) {
+        const float tmx = update_and_max(wbase, ndcr2, dci2, ndci2, rre, rim);
+        const uint32_t wmx = __reduce_max_sync(0xffffffffu, __float_as_uint(tmx));
+        if (l == 0) smax[w] = wmx;
+        __syncthreads();
+        uint32_t estar = smax[0];
+#pragma unroll
+        for (int i = 1; i < kWarps; ++i) estar = max(estar, smax[i]);
+
+        // Smallest linear index whose energy equals the maximum.
+        uint32_t kk = 0xffffffffu;
+        float cre = 0.f, cim = 0.f;
+        if (__float_as_uint(tmx) == estar) {
+#pragma unroll
+            for (int r = 7; r >= 0; --r) {
+                const float2 e = unpack2(energy2(rre[r], rim[r]));
+                const float2 re = unpack2(rre[r]), im = unpack2(rim[r]);
+                if (__float_as_uint(e.y) == estar) {
+                    kk = (uint32_t)((8 * w + r) * kDft + l + 32);
+                    cre = re.y;
+                    cim = im.y;
+                }
+                if (__float_as_uint(e.x) == estar) {
+                    kk = (uint32_t)((8 * w + r) * kDft + l);
+                    cre = re.x;
+                    cim = im.x;
+                }
+            }
+        }
+        const uint32_t wk = __reduce_min_sync(0xffffffffu, kk);
+        const uint32_t bal = __ballot_sync(0xffffffffu, kk == wk && wk != 0xffffffffu);
+        if (bal) {
+            const int src_lane = __ffs(bal) - 1;
+            cre = __shfl_sync(0xffffffffu, cre, src_lane);
+            cim = __shfl_sync(0xffffffffu, cim, src_lane);
+        }
+        if (l == 0) cand[w] = make_float4(__uint_as_float(wk), cre, cim, 0.f);
+        __syncthreads();
+        float4 best = cand[0];
+#pragma unroll
+        for (int i = 1; i < kWarps; ++i) {
+            const float4 c = cand[i];
+            if (__float_as_uint(c.x) < __float_as_uint(best.x)) best = c;
+        }
+        const uint32_t u = __float_as_uint(best.x);
+        const float dcr = best.y * gw, dci = best.z * gw;
+        if (tid == 0) {
+            dcl[it] = make_float2(dcr, dci);
+            ul[it] = (uint16_t)u;
+        }
+        ndcr2 = pack2(-dcr, -dcr);
+        dci2 = pack2(dci, dci);
+        ndci2 = pack2(-dci, -dci);
+        wbase = w4_base(w4addr, (int)(u >> 6), (int)(u & 63));
+    }
+
+    if (kTrace && tr.r) {  // residual after the last update (inspection only)
+        if (K > 0) update_and_max(wbase, ndcr2, dci2, ndci2, rre, rim);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const float2 re = unpack2(rre[r]), im = unpack2(rim[r]);
+            const int km = 8 * w + r;
+            tr.r[(km * kDft + l) * 2] = re.x;
+            tr.r[(km * kDft + l) * 2 + 1] = im.x;
+            tr.r[(km * kDft + l + 32) * 2] = re.y;
+            tr.r[(km * kDft + l + 32) * 2 + 1] = im.y;
+        }
+    }
+    __syncthreads();  // list complete
+    if (kTrace && (tr.u || tr.dc)) {
+        for (int it = tid; it < kp.iters; it += kThreads) {
+            if (tr.u) tr.u[it] = (it < K) ? (int32_t)ul[it] : -1;
+            if (tr.dc) {
+                const float2 d = (it < K) ? dcl[it] : make_float2(0.f, 0.f);
+                tr.dc[2 * it] = d.x;
+                tr.dc[2 * it + 1] = d.y;
+            }
+        }
+    }
+
+    // Eq. (1) on the centre block: Re sum_i dc_i exp(+j 2 pi (u_m m + u_n n)/64),
+    // compensated (Kahan) summation in FP32.
+    const int m = kBorder + (tid >> 4), n = kBorder + (tid & 15);
+    float s = 0.f, c = 0.f;
+    for (int it = 0; it < K; ++it) {
+        const float2 d = dcl[it];
+        const int u = ul[it];
+        const float2 cs = tw[((u >> 6) * m + (u & 63) * n) & (kDft - 1)];
+        const float term = fmaf(d.x, cs.x, -d.y * cs.y);
+        const float yv = term - c;
+        const float t = s + yv;
+        c = (t - s) - yv;
+        s = t;
+    }
+    return s;
+}
+
+// ---- kernels -------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kThreads, 3)
+k_group(const FrameDesc *frames, const int2 *items, KParams kp, const float *rho_tab,
+        const float2 *tw_tab) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int2 item = items[blockIdx.x];
+    const FrameDesc &fd = frames[item.x];
+    const FrameSrc src(fd, item.y);
+    const float g = run_block<false>(src, kp, rho_tab, tw_tab, smem, Trace{nullptr, nullptr, nullptr});
+    src.store(g);
+}
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__global__ void __launch_bounds__(kThreads, 3)
+k_persistent(const FrameDesc *frames, DepGraph dg, KParams kp, const float *rho_tab,
+             const float2 *tw_tab) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_item, s_ok;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int i = atomicAdd(dg.head, 1);
+            int ok = 1;
+            if (i < dg.n) {
+                long long spins = 0;
+                while (ld_acquire(dg.deps + i) > 0) {
+                    if (++spins > dg.spin_limit) {
+                        atomicExch(dg.error, FSE_ETIMEDOUT);
+                        ok = 0;
+                        break;
+                    }
+                    if ((spins & 255) == 0 && *(volatile int *)dg.error) {
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(200);
+                }
+            }
+            s_item = i;
+            s_ok = ok;
+        }
+        __syncthreads();
+        const int i = s_item;
+        if (i >= dg.n || !s_ok) break;
+        const int2 item = dg.items[i];
+        const FrameDesc &fd = frames[item.x];
+        const FrameSrc src(fd, item.y);
+        const float g = run_block<false>(src, kp, rho_tab, tw_tab, smem, Trace{nullptr, nullptr, nullptr});
+        src.store(g);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int s = dg.succ_ptr[i]; s < dg.succ_ptr[i + 1]; ++s)
+                atomicSub(dg.deps + dg.succ[s], 1);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 3)
+k_areas(const float *area_f, const uint8_t *area_cls, KParams kp, const float *rho_tab,
+        const float2 *tw_tab, float *g_out, int32_t *u_out, float *dc_out, float *r_out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const size_t a = blockIdx.x;
+    const AreaSrc src{area_f + a * kArea * kArea, area_cls + a * kArea * kArea,
+                      g_out + a * kBlock * kBlock};
+    const Trace tr{u_out ? u_out + a * kp.iters : nullptr,
+                   dc_out ? dc_out + a * kp.iters * 2 : nullptr,
+                   r_out ? r_out + a * kDft * kDft * 2 : nullptr};
+    const float g = run_block<true>(src, kp, rho_tab, tw_tab, smem, tr);
+    src.store(g);
+}
+
+// Block-loss map: one thread per (frame, sample row, block column) scans the
+// 16 samples of that block row.
+__global__ void k_block_loss(const FrameDesc *frames, uint8_t *lost, const int *lost_off) {
+    const FrameDesc &fd = frames[blockIdx.y];
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= fd.H * fd.bw) return;
+    const int y = idx / fd.bw, bx = idx - y * fd.bw;
+    const uint8_t *row = fd.mask + (size_t)y * fd.stride + bx * kBlock;
+    const int n = min(kBlock, fd.W - bx * kBlock);
+    int any = 0;
+    for (int i = 0; i < n; ++i) any |= row[i];
+    if (any) lost[lost_off[blockIdx.y] + (y / kBlock) * fd.bw + bx] = 1;
+}
+
+}  // namespace
+
+// ---- launchers ------------------------------------------------------------------
+
+static bool g_attr_done = false;
+
+static cudaError_t ensure_attrs() {
+    if (g_attr_done) return cudaSuccess;
+    const int max_smem = smem_bytes(FSE_MAX_ITERS);
+    cudaError_t e;
+    e = cudaFuncSetAttribute(k_group, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_areas, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e != cudaSuccess) return e;
+    g_attr_done = true;
+    return cudaSuccess;
+}
+
+bool precision_supported(int precision) { return precision == FSE_PREC_FP32; }
+
+int max_resident_ctas(int iters) {
+    if (ensure_attrs() != cudaSuccess) return 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent, kThreads,
+                                                      smem_bytes(iters)) != cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_block_loss(const FrameDesc *frames_dev, int n_frames, int max_rows_x_bw,
+                              uint8_t *lost_out, const int *lost_off_dev,
+                              cudaStream_t stream) {
+    if (n_frames <= 0 || max_rows_x_bw <= 0) return cudaSuccess;
+    dim3 grid((max_rows_x_bw + 255) / 256, n_frames);
+    k_block_loss<<<grid, 256, 0, stream>>>(frames_dev, lost_out, lost_off_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_frames(const FrameDesc *, int, int, cudaStream_t) {
+    return cudaSuccess;
+}
+
+cudaError_t launch_group(const FrameDesc *frames_dev, const int2 *items, int n_items,
+                         const KParams &kp, const float *rho_tab, const float2 *tw_tab,
+                         int precision, cudaStream_t stream) {
+    if (!precision_supported(precision)) return cudaErrorInvalidValue;
+    cudaError_t e = ensure_attrs();
+    if (e != cudaSuccess) return e;
+    if (n_items <= 0) return cudaSuccess;
+    k_group<<<n_items, kThreads, smem_bytes(kp.iters), stream>>>(frames_dev, items, kp,
+                                                                 rho_tab, tw_tab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_persistent(const FrameDesc *frames_dev, const DepGraph &dg,
+                              const KParams &kp, const float *rho_tab, const float2 *tw_tab,
+                              int precision, int grid, cudaStream_t stream) {
+    if (!precision_supported(precision)) return cudaErrorInvalidValue;
+    cudaError_t e = ensure_attrs();
+    if (e != cudaSuccess) return e;
+    if (dg.n <= 0) return cudaSuccess;
+    k_persistent<<<grid, kThreads, smem_bytes(kp.iters), stream>>>(frames_dev, dg, kp,
+                                                                   rho_tab, tw_tab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_areas(const float *area_f, const uint8_t *area_cls, int n,
+                         const KParams &kp, const float *rho_tab, const float2 *tw_tab,
+                         int precision, float *g_out, int32_t *u_out, float *dc_out,
+                         float *r_out, cudaStream_t stream) {
+    if (!precision_supported(precision)) return cudaErrorInvalidValue;
+    cudaError_t e = ensure_attrs();
+    if (e != cudaSuccess) return e;
+    if (n <= 0) return cudaSuccess;
+    k_areas<<<n, kThreads, smem_bytes(kp.iters), stream>>>(area_f, area_cls, kp, rho_tab,
+                                                           tw_tab, g_out, u_out, dc_out, r_out);
+    return cudaGetLastError();
+}
+
+}  // namespace fse

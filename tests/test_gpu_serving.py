@@ -1,0 +1,112 @@
+"""Serving through fse_submit / fse_poll: continuous batching of requests of
+different frame sizes and loss patterns; every result is the same alone and
+in the mix, and matches the oracle on a sampled request."""
+import time
+
+import numpy as np
+import pytest
+
+import fse_synth
+from gpu_util import oracle_conceal
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fse():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2207_00233_gb300 import build
+    build.build()
+    import paper_2207_00233_gb300 as pkg
+    return pkg
+
+
+def _requests(n, sizes=((288, 352), (720, 1280), (288, 352), (1080, 1920))):
+    reqs = []
+    for i in range(n):
+        h, w = sizes[i % len(sizes)]
+        img, mask = fse_synth.random_frame(h, w, 0.05 + 0.45 * ((i * 37) % 10) / 10.0, 700 + i)
+        if i % 5 == 4:
+            lost = np.zeros(fse_synth.block_grid(h, w), np.uint8)
+            lost[2, :] = 1
+            mask = np.maximum(mask, fse_synth.blocks_to_pixel_mask(lost, h, w))
+        reqs.append((img, mask))
+    return reqs
+
+
+def test_results_same_alone_and_in_the_mix(fse):
+    params = fse.make_params(iters=60, order=fse.FSE_ORDER_OPTIMIZED,
+                             executor=fse.FSE_EXEC_PERSISTENT)
+    reqs = _requests(10)
+    with fse.Context(0) as ctx:
+        alone = []
+        for img, mask in reqs:
+            out = np.empty_like(img)
+            ctx.fse_conceal_batch_host([(img, mask, out)], params)
+            alone.append(out)
+        ctx.fse_ctx_set_option(fse.FSE_OPT_SERVE_SLOTS, 3)
+        ctx.fse_ctx_set_option(fse.FSE_OPT_SERVE_MAX_BATCH, 4)
+        outs = [np.full_like(img, 7) for img, _ in reqs]
+        tickets = []
+        for i, (img, mask) in enumerate(reqs):
+            t = ctx.fse_submit(img, mask, outs[i], params)
+            assert t > 0
+            tickets.append(t)
+            time.sleep(0.002)
+        ctx.fse_drain(60000)
+        stats = [ctx.fse_poll(t) for t in tickets]
+        assert all(s is not None and s.status == 0 for s in stats)
+        for i in range(len(reqs)):
+            assert np.array_equal(outs[i], alone[i]), i
+        assert max(s.batch_requests for s in stats) >= 2  # requests were batched
+        for s, (img, mask) in zip(stats, reqs):
+            assert s.lost_blocks == int(
+                (np.add.reduceat(np.add.reduceat(mask, np.arange(0, mask.shape[0], 16), 0),
+                                 np.arange(0, mask.shape[1], 16), 1) > 0).sum())
+            assert s.latency_ms >= s.queue_ms >= 0
+        with pytest.raises(fse.FseError):
+            ctx.fse_poll(tickets[0])  # released after completion
+    img, mask = reqs[0]
+    o_work, o_out, _ = oracle_conceal(img, mask, params)
+    lost = mask != 0
+    assert np.abs(outs[0][lost].astype(int) - np.rint(o_work[lost]).astype(int)).max() <= 1
+
+
+def test_mixed_parameters_are_batched_separately(fse):
+    reqs = _requests(4, sizes=((96, 128),))
+    pa = fse.make_params(iters=30)
+    pb = fse.make_params(iters=50, order=fse.FSE_ORDER_LINESCAN)
+    with fse.Context(0) as ctx:
+        ref = []
+        for i, (img, mask) in enumerate(reqs):
+            out = np.empty_like(img)
+            ctx.fse_conceal_batch_host([(img, mask, out)], pa if i % 2 == 0 else pb)
+            ref.append(out)
+        outs = [np.empty_like(img) for img, _ in reqs]
+        ts = [ctx.fse_submit(img, mask, outs[i], pa if i % 2 == 0 else pb)
+              for i, (img, mask) in enumerate(reqs)]
+        ctx.fse_drain(30000)
+        for t in ts:
+            assert ctx.fse_poll(t).status == 0
+        for a, b in zip(outs, ref):
+            assert np.array_equal(a, b)
+
+
+def test_memory_budget_admission(fse):
+    """A small budget serialises batches but every request completes; a
+    request that can never fit fails with FSE_ENOMEM instead of waiting."""
+    reqs = _requests(6, sizes=((288, 352),))
+    params = fse.make_params(iters=20)
+    with fse.Context(0, mem_budget=8 << 20) as ctx:
+        outs = [np.empty_like(img) for img, _ in reqs]
+        ts = [ctx.fse_submit(img, mask, outs[i], params) for i, (img, mask) in enumerate(reqs)]
+        ctx.fse_drain(60000)
+        st = [ctx.fse_poll(t) for t in ts]
+        assert all(s.status == 0 for s in st)
+        big, bmask = fse_synth.random_frame(2160, 3840, 0.2, 99)
+        bout = np.empty_like(big)
+        t = ctx.fse_submit(big, bmask, bout, params)
+        ctx.fse_drain(60000)
+        assert ctx.fse_poll(t).status == 2
