@@ -201,6 +201,14 @@ int fse_last_kernel_ms(fse_ctx *ctx, float *ms);
 int fse_copy_work(fse_ctx *ctx, int frame, float *dst, int dst_stride,
                   void *cuda_stream);
 
+/* Copy the selection trace of frame `frame` of the last batch into dst
+ * (DEVICE pointer, [bh*bw][iters] int16, blocks in raster order): for every
+ * concealed block the K selected indices 64*k_m + k_n in iteration order,
+ * -1 when its area had no support; rows of blocks without loss are
+ * unspecified.  Only recorded while FSE_OPT_KEEP_TRACE is 1.
+ * Errors: FSE_EINVAL for a bad index, NULL dst or no recorded trace. */
+int fse_copy_trace(fse_ctx *ctx, int frame, int16_t *dst, void *cuda_stream);
+
 /* Context options (host-side settings; take effect on the next batch).
  *   FSE_OPT_SPIN_LIMIT       polls a device-side dependency wait makes
  *                            before it gives up with FSE_ETIMEDOUT
@@ -213,12 +221,15 @@ int fse_copy_work(fse_ctx *ctx, int frame, float *dst, int dst_stride,
  *   FSE_OPT_TEST_STUCK_DEP   test hook: 1 adds a dependency that nothing
  *                            releases to the last work item of the next
  *                            persistent batch, so its bounded wait runs out
+ *   FSE_OPT_KEEP_TRACE       1 records the selection trace of every block
+ *                            (see fse_copy_trace); 0 (default) does not
  * Errors: FSE_EINVAL for an unknown option or value. */
 #define FSE_OPT_SPIN_LIMIT 1
 #define FSE_OPT_PERSISTENT_CTAS 2
 #define FSE_OPT_SERVE_SLOTS 3
 #define FSE_OPT_SERVE_MAX_BATCH 4
 #define FSE_OPT_TEST_STUCK_DEP 5
+#define FSE_OPT_KEEP_TRACE 6
 int fse_ctx_set_option(fse_ctx *ctx, int option, long long value);
 
 const char *fse_strerror(int status);

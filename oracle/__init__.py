@@ -55,7 +55,7 @@ def lib() -> ctypes.CDLL:
         L.oracle_conceal_frame.argtypes = [
             ctypes.c_int, ctypes.c_int, _u8p, _u8p, ctypes.c_int, ctypes.c_int,
             ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-            ctypes.c_int, ctypes.c_int, _f64p, _u8p, _OptPtr]
+            ctypes.c_int, ctypes.c_int, _f64p, _u8p, _OptPtr, _OptPtr]
         L.oracle_conceal_frame.restype = ctypes.c_int
         L.oracle_max_threads.argtypes = []
         L.oracle_max_threads.restype = ctypes.c_int
@@ -136,9 +136,11 @@ def extrapolate_area(f: np.ndarray, cls: np.ndarray, F: int, K: int, rho: float,
 
 def conceal_frame(img: np.ndarray, mask: np.ndarray, *, block: int = 16, border: int = 16,
                   dft: int = 64, iters: int = 200, rho: float = 0.7, delta: float = 0.2,
-                  gamma: float = 0.5, order: int = ORDER_OPTIMIZED, threads: int = 1):
+                  gamma: float = 0.5, order: int = ORDER_OPTIMIZED, threads: int = 1,
+                  trace: bool = False):
     """Conceal one frame.  Returns (work FP64 [H,W], out uint8 [H,W],
-    group_of_block int32 [BH,BW])."""
+    group_of_block int32 [BH,BW]), plus the selection trace
+    [BH*BW, iters] int32 (-2 for blocks without loss) when ``trace``."""
     img = np.ascontiguousarray(img, dtype=np.uint8)
     mask = np.ascontiguousarray(mask, dtype=np.uint8)
     H, Wd = img.shape
@@ -148,9 +150,12 @@ def conceal_frame(img: np.ndarray, mask: np.ndarray, *, block: int = 16, border:
     work = np.empty((H, Wd), np.float64)
     out = np.empty((H, Wd), np.uint8)
     gob = np.empty((bh, bw), np.int32)
+    ut = np.full((bh * bw, max(iters, 1)), -2, np.int32) if trace else None
     rc = lib().oracle_conceal_frame(H, Wd, img.ravel(), mask.ravel(), block, border, dft,
                                     iters, rho, delta, gamma, int(order), int(threads),
-                                    work.ravel(), out.ravel(), gob)
+                                    work.ravel(), out.ravel(), gob, ut)
     if rc:
         raise ValueError(f"oracle_conceal_frame failed ({rc})")
+    if trace:
+        return work, out, gob, ut[:, :iters]
     return work, out, gob

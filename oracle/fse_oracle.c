@@ -404,7 +404,7 @@ int oracle_conceal_frame(int H, int Wd, const uint8_t *img,
                          const uint8_t *mask, int B, int d, int F, int K,
                          double rho, double delta, double gamma, int order,
                          int threads, double *work, uint8_t *out,
-                         int32_t *group_of_block_out)
+                         int32_t *group_of_block_out, int32_t *u_trace)
 {
     if (H <= 0 || Wd <= 0 || B <= 0 || d < 0 || !img || !mask || !work || !out)
         return -1;
@@ -479,8 +479,9 @@ int oracle_conceal_frame(int H, int Wd, const uint8_t *img,
                         cls[idx] = ORACLE_CLS_BO;
                     }
                 }
+            int32_t *ut = u_trace ? u_trace + (size_t)b * (size_t)K : NULL;
             int r = oracle_extrapolate_area(M, M, F, f, cls, rho, delta, gamma, K,
-                                            0, want, gv, NULL, NULL, NULL, NULL,
+                                            0, want, gv, NULL, NULL, NULL, ut,
                                             NULL, NULL, NULL);
             if (r)
                 err |= 1;

@@ -51,12 +51,14 @@ int oracle_extrapolate_area(int M, int N, int F, const double *f,
 /* Whole frame.  img, mask: [H*Wd] uint8 (mask 1 = lost sample).  Block size
  * B, border d (area M = B + 2d <= F).  threads: OpenMP threads over the
  * blocks of a group.  work [H*Wd] FP64 working frame, out [H*Wd] uint8,
- * group_of_block_out [bh*bw] (optional). */
+ * group_of_block_out [bh*bw] (optional), u_trace [bh*bw][K] (optional): the
+ * selected indices of every concealed block (rows of other blocks are left
+ * untouched). */
 int oracle_conceal_frame(int H, int Wd, const uint8_t *img,
                          const uint8_t *mask, int B, int d, int F, int K,
                          double rho, double delta, double gamma, int order,
                          int threads, double *work, uint8_t *out,
-                         int32_t *group_of_block_out);
+                         int32_t *group_of_block_out, int32_t *u_trace);
 
 int oracle_max_threads(void);
 

@@ -23,10 +23,10 @@ FSE_MAX_ITERS = 1024
 EXPORTED = [
     "fse_plan_order", "fse_ctx_create", "fse_ctx_destroy", "fse_conceal_batch",
     "fse_conceal_batch_host", "fse_extrapolate_areas", "fse_submit", "fse_poll",
-    "fse_drain", "fse_last_batch_info", "fse_ctx_set_option", "fse_copy_work", "fse_last_kernel_ms", "fse_strerror",
+    "fse_drain", "fse_last_batch_info", "fse_ctx_set_option", "fse_copy_work", "fse_copy_trace", "fse_last_kernel_ms", "fse_strerror",
 ]
 FSE_OPT_SPIN_LIMIT, FSE_OPT_PERSISTENT_CTAS, FSE_OPT_SERVE_SLOTS = 1, 2, 3
-FSE_OPT_SERVE_MAX_BATCH, FSE_OPT_TEST_STUCK_DEP = 4, 5
+FSE_OPT_SERVE_MAX_BATCH, FSE_OPT_TEST_STUCK_DEP, FSE_OPT_KEEP_TRACE = 4, 5, 6
 
 
 class fse_params(ctypes.Structure):
@@ -84,6 +84,7 @@ def lib() -> ctypes.CDLL:
                                       ctypes.POINTER(cint)]
     L.fse_ctx_set_option.argtypes = [vp, cint, ctypes.c_longlong]
     L.fse_copy_work.argtypes = [vp, cint, vp, cint, vp]
+    L.fse_copy_trace.argtypes = [vp, cint, vp, vp]
     L.fse_last_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     L.fse_strerror.argtypes = [cint]
     L.fse_strerror.restype = ctypes.c_char_p
@@ -244,6 +245,11 @@ class Context:
 
     def fse_drain(self, timeout_ms: int = -1) -> None:
         _check(lib().fse_drain(self.handle, int(timeout_ms)), "fse_drain")
+
+    def fse_copy_trace(self, frame: int, dst, stream=None) -> None:
+        """dst: CUDA int16 tensor with bh*bw*iters elements."""
+        _check(lib().fse_copy_trace(self.handle, int(frame), dst.data_ptr(),
+                                    _stream_handle(stream)), "fse_copy_trace")
 
     def fse_last_kernel_ms(self) -> float:
         ms = ctypes.c_float(0.0)

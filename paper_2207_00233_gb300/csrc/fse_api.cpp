@@ -8,6 +8,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -214,6 +215,9 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
     const int nblocks = lost_off[n];
 
     rc = ctx->dev_reserve(ws.frames, sizeof(FrameDesc) * n);
+    if (!rc && ctx->keep_trace)
+        rc = ctx->dev_reserve(ws.trace, sizeof(int16_t) * std::max<size_t>(
+                                            (size_t)nblocks * std::max(p->iters, 1), 1));
     if (!rc) rc = ctx->dev_reserve(ws.work, sizeof(float) * work_floats);
     if (!rc) rc = ctx->dev_reserve(ws.lost, nblocks);
     if (!rc) rc = ctx->dev_reserve(ws.lost_off, sizeof(int) * (n + 1));
@@ -225,6 +229,9 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
         for (int i = 0; i < n; ++i) {
             fd[i].work = wp;
             fd[i].gob = static_cast<int32_t *>(ws.gob.ptr) + lost_off[i];
+            fd[i].trace = ctx->keep_trace ? static_cast<int16_t *>(ws.trace.ptr) +
+                                                (size_t)lost_off[i] * p->iters
+                                          : nullptr;
             wp += (size_t)fd[i].H * fd[i].wstride;
         }
     }
@@ -269,22 +276,41 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
         return FSE_ETIMEDOUT;
     }
 
-    // ---- processing order per frame (host, integer) ----
-    std::vector<int32_t> gob_h(nblocks), gptr, ids;
+    // ---- processing order per frame (host, integer; frames in parallel) ----
+    std::vector<int32_t> gob_h(nblocks);
     std::vector<std::vector<int32_t>> frame_gptr(n), frame_ids(n);
-    int max_groups = 0, lost_blocks = 0;
-    for (int i = 0; i < n; ++i) {
+    std::vector<int> plan_rc(n, FSE_OK);
+    auto plan_one = [&](int i) {
         const int nb = fd[i].bh * fd[i].bw;
-        gptr.assign(nb + 1, 0);
-        ids.assign(nb, 0);
+        std::vector<int32_t> gptr(nb + 1, 0), ids(nb, 0);
         int32_t ng = 0;
-        rc = fse_plan_order(fd[i].bw, fd[i].bh, lost_h.data() + lost_off[i], p->order,
-                            gob_h.data() + lost_off[i], gptr.data(), ids.data(), &ng);
-        if (rc) return rc;
+        plan_rc[i] = fse_plan_order(fd[i].bw, fd[i].bh, lost_h.data() + lost_off[i], p->order,
+                                    gob_h.data() + lost_off[i], gptr.data(), ids.data(), &ng);
+        if (plan_rc[i]) return;
         frame_gptr[i].assign(gptr.begin(), gptr.begin() + ng + 1);
         frame_ids[i].assign(ids.begin(), ids.begin() + gptr[ng]);
-        max_groups = std::max(max_groups, (int)ng);
-        lost_blocks += gptr[ng];
+    };
+    {
+        const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+        const int nt = std::min(n, hw);
+        if (nt <= 1) {
+            for (int i = 0; i < n; ++i) plan_one(i);
+        } else {
+            std::atomic<int> next{0};
+            std::vector<std::thread> pool;
+            for (int t = 0; t < nt; ++t)
+                pool.emplace_back([&] {
+                    for (int i = next++; i < n; i = next++) plan_one(i);
+                });
+            for (auto &th : pool) th.join();
+        }
+    }
+    int max_groups = 0, lost_blocks = 0;
+    for (int i = 0; i < n; ++i) {
+        if (plan_rc[i]) return plan_rc[i];
+        const int ng = (int)frame_gptr[i].size() - 1;
+        max_groups = std::max(max_groups, ng);
+        lost_blocks += frame_gptr[i][ng];
     }
 
     // ---- work items ----
@@ -365,7 +391,7 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
     rc = put(ws.frames.ptr, fd.data(), sizeof(FrameDesc) * n);
     if (!rc) rc = put(ws.gob.ptr, gob_h.data(), sizeof(int32_t) * nblocks);
     if (!rc) rc = put(ws.items.ptr, items.data(), sizeof(int2) * n_items);
-    if (!rc && persistent) {
+    if (!rc && persistent && n_items > 0) {
         rc = put(ws.deps.ptr, deps.data(), sizeof(int) * n_items);
         if (!rc) rc = put(ws.succ_ptr.ptr, succ_ptr.data(), sizeof(int) * (n_items + 1));
         if (!rc) rc = put(ws.succ.ptr, succ.data(), sizeof(int) * succ.size());
@@ -427,6 +453,12 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
     ws.lost_blocks = lost_blocks;
     ws.groups = max_groups;
     ws.launches = launches;
+    ws.trace_ptr.assign(n, nullptr);
+    ws.trace_len.assign(n, 0);
+    for (int i = 0; i < n; ++i) {
+        ws.trace_ptr[i] = fd[i].trace;
+        ws.trace_len[i] = fd[i].trace ? (size_t)fd[i].bh * fd[i].bw * p->iters : 0;
+    }
     ws.work_ptr.resize(n);
     ws.work_w.resize(n);
     ws.work_h.resize(n);
@@ -465,6 +497,7 @@ void fse::release_workspace(fse_ctx *ctx, Workspace &ws) {
     ctx->dev_release(ws.succ_ptr);
     ctx->dev_release(ws.succ);
     ctx->dev_release(ws.status);
+    ctx->dev_release(ws.trace);
     ctx->dev_release(ws.d_luma);
     ctx->dev_release(ws.d_mask);
     ctx->dev_release(ws.d_out);
@@ -644,9 +677,25 @@ extern "C" int fse_copy_work(fse_ctx *ctx, int frame, float *dst, int dst_stride
     return FSE_OK;
 }
 
+extern "C" int fse_copy_trace(fse_ctx *ctx, int frame, int16_t *dst, void *cuda_stream) {
+    if (!ctx || !dst) return FSE_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    const Workspace &ws = ctx->ws;
+    if (frame < 0 || frame >= (int)ws.trace_ptr.size() || !ws.trace_ptr[frame])
+        return FSE_EINVAL;
+    cudaSetDevice(ctx->device);
+    CK(cudaMemcpyAsync(dst, ws.trace_ptr[frame], sizeof(int16_t) * ws.trace_len[frame],
+                       cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(cuda_stream)));
+    return FSE_OK;
+}
+
 extern "C" int fse_ctx_set_option(fse_ctx *ctx, int option, long long value) {
     if (!ctx) return FSE_EINVAL;
     switch (option) {
+    case FSE_OPT_KEEP_TRACE:
+        if (value != 0 && value != 1) return FSE_EINVAL;
+        ctx->keep_trace = value != 0;
+        return FSE_OK;
     case FSE_OPT_SPIN_LIMIT:
         if (value < 1) return FSE_EINVAL;
         ctx->spin_limit = value;

@@ -27,7 +27,7 @@ struct HostBuf {
 
 // Everything one in-flight batch needs on the device.
 struct Workspace {
-    DevBuf frames, work, lost, lost_off, gob, items, deps, succ_ptr, succ, status;
+    DevBuf frames, work, lost, lost_off, gob, items, deps, succ_ptr, succ, status, trace;
     DevBuf d_luma, d_mask, d_out;  // device copies of host frames
     HostBuf stage;                 // pinned staging for uploads / readback
     HostBuf io;                    // pinned staging of serving frames
@@ -36,7 +36,9 @@ struct Workspace {
     bool k_timed = false;
     bool status_live = false;      // status word of a persistent launch pending
     int lost_blocks = 0, groups = 0, launches = 0;  // of the last batch
-    std::vector<float *> work_ptr;                  // per frame of the last batch
+    std::vector<int16_t *> trace_ptr;               // per frame of the last batch
+    std::vector<size_t> trace_len;
+    std::vector<float *> work_ptr;
     std::vector<int> work_w, work_h, work_stride;
 };
 
@@ -72,6 +74,7 @@ struct fse_ctx {
     long long spin_limit = 1LL << 23;
     int persistent_ctas = 0;   // per SM; 0 = occupancy limit
     bool test_stuck_dep = false;
+    bool keep_trace = false;
 
     fse::DevBuf tw_dev;                                   // 64 twiddles
     std::vector<std::pair<float, fse::DevBuf>> rho_tabs;  // Eq. (2) decay per rho

@@ -56,7 +56,7 @@ struct FrameDesc {
     float *work;             // [H][wstride] FP32 working frame
     const int32_t *gob;      // [bh][bw] group of each block, -1 = no loss
     int H, W, stride, wstride, bh, bw;
-    int pad0, pad1;
+    int16_t *trace;          // [bh*bw][iters] selected indices, or null
 };
 
 // Dependency graph of the persistent executor: items are (frame, block)

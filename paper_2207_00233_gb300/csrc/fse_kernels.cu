@@ -391,6 +391,19 @@ __device__ __forceinline__ float run_block(const Src &src, const KParams &kp,
 
 // ---- kernels -------------------------------------------------------------------
 
+// Selection trace of a frame block (inspection option): the K selected
+// indices from the shared list, -1 when the area had no support.  Runs after
+// run_block, whose last barrier completed the list.
+__device__ __forceinline__ void write_frame_trace(const FrameDesc &fd, int block,
+                                                  const KParams &kp, const unsigned char *smem) {
+    if (!fd.trace) return;
+    const float W0 = reinterpret_cast<const float *>(smem + kRedOff + 32 + 128)[0];
+    const uint16_t *ul = reinterpret_cast<const uint16_t *>(smem + kListOff + kp.iters * 8);
+    int16_t *t = fd.trace + (size_t)block * kp.iters;
+    for (int it = threadIdx.x; it < kp.iters; it += kThreads)
+        t[it] = (W0 > 0.f) ? (int16_t)ul[it] : (int16_t)-1;
+}
+
 __global__ void __launch_bounds__(kThreads, 3)
 k_group(const FrameDesc *frames, const int2 *items, KParams kp, const float *rho_tab,
         const float2 *tw_tab) {
@@ -400,6 +413,7 @@ k_group(const FrameDesc *frames, const int2 *items, KParams kp, const float *rho
     const FrameSrc src(fd, item.y);
     const float g = run_block<false>(src, kp, rho_tab, tw_tab, smem, Trace{nullptr, nullptr, nullptr});
     src.store(g);
+    write_frame_trace(fd, item.y, kp, smem);
 }
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
@@ -443,6 +457,7 @@ k_persistent(const FrameDesc *frames, DepGraph dg, KParams kp, const float *rho_
         const FrameSrc src(fd, item.y);
         const float g = run_block<false>(src, kp, rho_tab, tw_tab, smem, Trace{nullptr, nullptr, nullptr});
         src.store(g);
+        write_frame_trace(fd, item.y, kp, smem);
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {

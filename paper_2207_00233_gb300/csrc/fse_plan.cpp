@@ -6,6 +6,7 @@
 // cells hold a sentinel that is never selected and never decremented.
 #include <cstdint>
 #include <cstring>
+#include <set>
 #include <vector>
 
 #include "../../include/fse.h"
@@ -70,16 +71,24 @@ extern "C" int fse_plan_order(int bw, int bh, const uint8_t *block_lost,
                 for (int dx = -1; dx <= 1; ++dx)
                     if (dy | dx) G.at(by + dy, bx + dx) += 1;  // padding stays very negative
         }
-    // Second pass: blocks with nothing to extrapolate are marked -1.
+    // Second pass: blocks with nothing to extrapolate are marked -1.  The
+    // others go into buckets by their count, each bucket ordered by raster
+    // index, so that a round visits exactly the blocks with N = N_min in
+    // scan order without rescanning the grid.
+    std::vector<std::set<int>> bucket;
     int pending = 0;
     for (int by = 0; by < bh; ++by)
         for (int bx = 0; bx < bw; ++bx) {
-            if (!block_lost[by * bw + bx]) {
+            const int b = by * bw + bx;
+            if (!block_lost[b]) {
                 G.at(by, bx) = -1;
-                group_of_block[by * bw + bx] = -1;
-            } else {
-                ++pending;
+                group_of_block[b] = -1;
+                continue;
             }
+            const int v = G.at(by, bx);
+            if (v >= (int)bucket.size()) bucket.resize(v + 1);
+            bucket[v].insert(b);
+            ++pending;
         }
 
     // Membership of the set S under construction, padded like G.
@@ -91,32 +100,31 @@ extern "C" int fse_plan_order(int bw, int bh, const uint8_t *block_lost,
     int32_t g = 0, pos = 0;
     group_ptr[0] = 0;
     std::vector<int> members;
+    int nmin = 0;
     while (pending > 0) {
-        // N_min: smallest count among blocks still to do (count >= 0).
-        int nmin = -1;
-        for (int by = 0; by < bh; ++by)
-            for (int bx = 0; bx < bw; ++bx) {
-                const int v = G.at(by, bx);
-                if (v >= 0 && (nmin < 0 || v < nmin)) nmin = v;
-            }
-        // S: raster scan; a block joins when it has N_min and none of its
-        // neighbours joined before it.  Only the left and the three upper
-        // neighbours can have joined earlier in the scan.
+        // N_min: smallest count among blocks still to do.  Counts only
+        // decrease, but a decrement can refill a lower bucket, so search
+        // from 0 each round (there are at most 14 buckets).
+        nmin = 0;
+        while (bucket[nmin].empty()) ++nmin;
+        // S: raster scan over the blocks with N_min; a block joins when none
+        // of its neighbours joined before it.  Only the left and the three
+        // upper neighbours can have joined earlier in the scan.
         members.clear();
-        for (int by = 0; by < bh; ++by)
-            for (int bx = 0; bx < bw; ++bx) {
-                if (G.at(by, bx) != nmin) continue;
-                if (s_at(by, bx - 1) | s_at(by - 1, bx - 1) | s_at(by - 1, bx) |
-                    s_at(by - 1, bx + 1))
-                    continue;
-                s_at(by, bx) = 1;
-                members.push_back(by * bw + bx);
-            }
+        for (int b : bucket[nmin]) {
+            const int by = b / bw, bx = b % bw;
+            if (s_at(by, bx - 1) | s_at(by - 1, bx - 1) | s_at(by - 1, bx) |
+                s_at(by - 1, bx + 1))
+                continue;
+            s_at(by, bx) = 1;
+            members.push_back(b);
+        }
         // Extrapolation of S, then the count updates of Algorithm 1.
         for (int b : members) {
             const int by = b / bw, bx = b % bw;
             block_ids[pos++] = b;
             group_of_block[b] = g;
+            bucket[nmin].erase(b);
             G.at(by, bx) = -1;
             s_at(by, bx) = 0;
             for (int dy = -1; dy <= 1; ++dy)
@@ -125,7 +133,12 @@ extern "C" int fse_plan_order(int bw, int bh, const uint8_t *block_lost,
                     // Only blocks still to do are decremented; finished
                     // blocks (-1) and padding keep their value.
                     int &v = G.at(by + dy, bx + dx);
-                    if (v >= 0) --v;
+                    if (v >= 0) {
+                        const int nb_idx = (by + dy) * bw + (bx + dx);
+                        bucket[v].erase(nb_idx);
+                        --v;
+                        bucket[v].insert(nb_idx);
+                    }
                 }
         }
         pending -= (int)members.size();

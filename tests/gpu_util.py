@@ -5,20 +5,32 @@ Tolerance (floating point): every concealed sample's FP32 working value is
 within 0.5 of the oracle's FP64 value on the 8-bit scale, and the PSNR of the
 concealed samples against the oracle is at least 50 dB.  The 8-bit output is
 checked in the kernel's own precision: out == round-half-even(FP32 value).
+
+The argmax of every iteration is a decision taken in floating point.  Where
+the FP32 and FP64 energies of two candidates are closer than FP32 can
+resolve, the two sides may pick different members of the near-tie, and from
+there on (in that block and in blocks that read it as reconstructed area)
+the extrapolated values are not unique.  Such blocks are checked for
+validity (fse_check): the divergence starts at a near-tie of the oracle's
+own trajectory, and the GPU result is a correct FSE trajectory on the
+samples it saw.  All other blocks are compared with the oracle sample by
+sample.
 """
 from __future__ import annotations
 
 import numpy as np
 
 import oracle
+from fse_check import area_from_frame, near_tie_at_divergence, trajectory
 
 TOL_ABS = 0.5
 TOL_PSNR_DB = 50.0
 
 
-def gpu_conceal(ctx, frames, params, want_work=True):
+def gpu_conceal(ctx, frames, params, want_work=True, want_trace=False):
     """frames: list of (img uint8, mask uint8).  Returns lists of outputs
-    (uint8) and FP32 working frames (NaN where not lost)."""
+    (uint8), FP32 working frames (NaN where not lost) and, if asked, the
+    selection traces [BH*BW, K] int16."""
     import torch
     dev = torch.device("cuda:0")
     tens = []
@@ -27,7 +39,7 @@ def gpu_conceal(ctx, frames, params, want_work=True):
         m = torch.from_numpy(np.ascontiguousarray(mask)).to(dev)
         tens.append((l, m, torch.empty_like(l)))
     ctx.fse_conceal_batch(tens, params)
-    outs, works = [], []
+    outs, works, traces = [], [], []
     for i, (l, m, o) in enumerate(tens):
         if want_work:
             wk = torch.empty(l.shape, dtype=torch.float32, device=dev)
@@ -36,18 +48,27 @@ def gpu_conceal(ctx, frames, params, want_work=True):
             w = wk.cpu().numpy().astype(np.float64)
             w[frames[i][1] == 0] = np.nan
             works.append(w)
+        if want_trace:
+            h, wd = l.shape
+            nb = ((h + 15) // 16) * ((wd + 15) // 16)
+            t = torch.empty(nb * max(params.iters, 1), dtype=torch.int16, device=dev)
+            ctx.fse_copy_trace(i, t)
+            torch.cuda.synchronize()
+            traces.append(t.cpu().numpy().astype(np.int32).reshape(nb, -1)[:, :params.iters])
         torch.cuda.synchronize()
         outs.append(o.cpu().numpy())
+    if want_trace:
+        return outs, works, traces
     return outs, works
 
 
-def oracle_conceal(img, mask, params, threads=None):
+def oracle_conceal(img, mask, params, threads=None, trace=False):
     if threads is None:
         threads = oracle.max_threads()
     return oracle.conceal_frame(img, mask, block=params.block, border=params.border,
                                 dft=params.dft, iters=params.iters, rho=params.rho,
                                 delta=params.delta, gamma=params.gamma, order=params.order,
-                                threads=threads)
+                                threads=threads, trace=trace)
 
 
 def psnr(a, b):
@@ -55,18 +76,89 @@ def psnr(a, b):
     return float("inf") if mse == 0 else 10 * np.log10(255.0 ** 2 / mse)
 
 
-def check_frame(img, mask, out, work, o_work, o_out, label=""):
+def check_output_basics(img, mask, out, work, label=""):
     lost = mask != 0
     assert np.array_equal(out[~lost], img[~lost]), f"{label}: known samples changed"
     if lost.any():
-        g = work[lost]
-        r = o_work[lost]
-        assert np.all(np.isfinite(g)), f"{label}: non-finite working values"
-        err = np.abs(g - r)
-        assert err.max() <= TOL_ABS, f"{label}: max |gpu - oracle| = {err.max():.4f}"
-        assert psnr(g, r) >= TOL_PSNR_DB, f"{label}: PSNR {psnr(g, r):.2f} dB"
-        # quantisation decided in the kernel's precision
+        assert np.all(np.isfinite(work[lost])), f"{label}: non-finite working values"
+        assert np.all((work[lost] >= 0) & (work[lost] <= 255))
         q = np.rint(work[lost].astype(np.float32)).astype(np.int64)
         assert np.array_equal(out[lost].astype(np.int64), q), f"{label}: out != rint(work)"
-        return float(err.max()), psnr(g, r)
-    return 0.0, float("inf")
+
+
+def compare_frame(img, mask, params, out, work, g_trace, o_work, o_trace, gob, label="",
+                  max_root_frac=0.1):
+    """Sample-by-sample parity on blocks whose selections and inputs agree
+    with the oracle; validity on the others.  Returns a statistics dict."""
+    check_output_basics(img, mask, out, work, label)
+    bh, bw = gob.shape
+    K = params.iters
+    lost_blocks = [(int(gob[by, bx]), by, bx) for by in range(bh) for bx in range(bw)
+                   if gob[by, bx] >= 0]
+    lost_blocks.sort()
+    clean = np.zeros((bh, bw), bool)
+    stats = dict(blocks=len(lost_blocks), clean=0, roots=0, downstream=0,
+                 max_err_clean=0.0, worst_tie=0.0, worst_valid=0.0, max_err_valid=0.0)
+    errs = []
+    for g, by, bx in lost_blocks:
+        b = by * bw + bx
+        same = np.array_equal(g_trace[b], o_trace[b])
+        up_clean = True
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                ny, nx = by + dy, bx + dx
+                if (dy or dx) and 0 <= ny < bh and 0 <= nx < bw:
+                    if 0 <= gob[ny, nx] < g and not clean[ny, nx]:
+                        up_clean = False
+        ys = slice(by * 16, min(by * 16 + 16, img.shape[0]))
+        xs = slice(bx * 16, min(bx * 16 + 16, img.shape[1]))
+        lm = mask[ys, xs] != 0
+        if same and up_clean:
+            clean[by, bx] = True
+            stats["clean"] += 1
+            e = np.abs(work[ys, xs][lm] - o_work[ys, xs][lm])
+            errs.append((work[ys, xs][lm], o_work[ys, xs][lm]))
+            stats["max_err_clean"] = max(stats["max_err_clean"], float(e.max()))
+            continue
+        # not unique: the GPU result must be a valid trajectory on its inputs
+        f, cls = area_from_frame(img, mask, work, gob, by, bx)
+        worst, gv = trajectory(f, cls, g_trace[b], params.rho, params.delta, params.gamma)
+        assert worst <= 1.0, f"{label}: block ({by},{bx}) selection off by {worst:.2f} tau"
+        gi = np.clip(gv, 0, 255)[:lm.shape[0], :lm.shape[1]]
+        ev = float(np.abs(gi[lm] - work[ys, xs][lm]).max())
+        assert ev <= TOL_ABS, f"{label}: block ({by},{bx}) model differs from its trajectory by {ev}"
+        stats["worst_valid"] = max(stats["worst_valid"], worst)
+        stats["max_err_valid"] = max(stats["max_err_valid"], ev)
+        if up_clean:
+            stats["roots"] += 1
+            fo, clso = area_from_frame(img, mask, o_work, gob, by, bx)
+            it, tie = near_tie_at_divergence(fo, clso, g_trace[b], o_trace[b], params.rho,
+                                             params.delta, params.gamma)
+            assert tie <= 1.0, f"{label}: block ({by},{bx}) diverged at it {it} by {tie:.2f} tau"
+            stats["worst_tie"] = max(stats["worst_tie"], tie)
+        else:
+            stats["downstream"] += 1
+    assert stats["max_err_clean"] <= TOL_ABS, f"{label}: {stats}"
+    if errs:
+        a = np.concatenate([x for x, _ in errs])
+        r = np.concatenate([y for _, y in errs])
+        stats["psnr_clean"] = psnr(a, r)
+        assert stats["psnr_clean"] >= TOL_PSNR_DB, f"{label}: {stats}"
+    if stats["blocks"]:
+        stats["diverged_frac"] = 1.0 - stats["clean"] / stats["blocks"]
+        # independent divergences are rare; each one was checked as a near-tie
+        assert stats["roots"] <= max(1, max_root_frac * stats["blocks"]), f"{label}: {stats}"
+    return stats
+
+
+def run_and_compare(ctx, frames, params, label="", sample=None, max_root_frac=0.1):
+    """GPU batch with traces, oracle per (sampled) frame, compare_frame."""
+    outs, works, traces = gpu_conceal(ctx, frames, params, want_trace=True)
+    all_stats = []
+    for i in (range(len(frames)) if sample is None else sample):
+        img, mask = frames[i]
+        o_work, o_out, gob, o_trace = oracle_conceal(img, mask, params, trace=True)
+        st = compare_frame(img, mask, params, outs[i], works[i], traces[i], o_work, o_trace, gob,
+                           f"{label} frame {i}", max_root_frac)
+        all_stats.append(st)
+    return outs, works, traces, all_stats
