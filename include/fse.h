@@ -104,6 +104,7 @@ typedef struct fse_stats {
     int lost_blocks;     /* blocks concealed                                  */
     int groups;          /* processing-order groups                           */
     int batch_requests;  /* requests in the device batch that carried it      */
+    int inflight;        /* other device batches in flight when it started    */
     double queue_ms;     /* submit -> start of its device batch               */
     double latency_ms;   /* submit -> result copied back                      */
 } fse_stats;

@@ -45,6 +45,7 @@ class fse_frame(ctypes.Structure):
 class fse_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("lost_blocks", ctypes.c_int),
                 ("groups", ctypes.c_int), ("batch_requests", ctypes.c_int),
+                ("inflight", ctypes.c_int),
                 ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
 
 

@@ -35,13 +35,21 @@ inline int smem_bytes(int iters) {
     return kListOff + iters * 8 + ((iters * 2 + 15) / 16) * 16;
 }
 
-// Scratch inside the W4 region before the iterations.
-constexpr int kXTileOff = 0;                                // 48x48 float: w*f
-constexpr int kWTileOff = kXTileOff + kArea * kArea * 4;    // 48x48 float: w
-constexpr int kHalfCols = kDft / 2 + 1;                     // 33 (real input)
-constexpr int kYxOff = kWTileOff + kArea * kArea * 4;       // 48x33 float2
-constexpr int kYwOff = kYxOff + kArea * kHalfCols * 8;      // 48x33 float2
+// Scratch inside the W4 region before the iterations.  The area tiles have
+// a row stride of 49 floats so that 32 consecutive rows of one column fall
+// into 32 different banks.
+constexpr int kTileStride = kArea + 1;                          // 49
+constexpr int kXTileOff = 0;                                    // 48x49 float: w*f
+constexpr int kWTileOff = kXTileOff + kArea * kTileStride * 4;  // 48x49 float: w
+constexpr int kHalfCols = kDft / 2 + 1;                         // 33 (real input)
+constexpr int kYxOff = kWTileOff + kArea * kTileStride * 4;     // 48x33 float2
+constexpr int kYwOff = kYxOff + kArea * kHalfCols * 8;          // 48x33 float2
 static_assert(kYwOff + kArea * kHalfCols * 8 <= kW4Bytes, "scratch overflow");
+// After the iterations the W4 region holds the synthesis tables, in chunks
+// of kSynChunk iterations: P[it][i] = dc_it exp(+j 2 pi u_m (16+i) / 64) and
+// E[it][j] = exp(+j 2 pi u_n (16+j) / 64), 16 complex values each.
+constexpr int kSynChunk = 256;
+static_assert(kSynChunk * 32 * 8 <= kW4Bytes, "synthesis tables overflow");
 
 struct KParams {
     float rho, delta, gamma;

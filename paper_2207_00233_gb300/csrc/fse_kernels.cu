@@ -52,6 +52,11 @@ __device__ __forceinline__ u64 mul2(u64 a, u64 b) {
 __device__ __forceinline__ u64 energy2(u64 re, u64 im) {
     return fma2(im, im, mul2(re, re));
 }
+__device__ __forceinline__ float max3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
 __device__ __forceinline__ void lds_pair(uint32_t addr, u64 &a, u64 &b) {
     asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
 }
@@ -93,8 +98,8 @@ struct FrameSrc {
                     }
                 }
             }
-            xt[p] = w * v;
-            wt[p] = w;
+            xt[m * kTileStride + n] = w * v;
+            wt[m * kTileStride + n] = w;
         }
     }
 
@@ -119,12 +124,13 @@ struct AreaSrc {
 
     __device__ void gather(float *xt, float *wt, const float *rho_tab, float delta) const {
         for (int p = threadIdx.x; p < kArea * kArea; p += kThreads) {
+            const int m = p / kArea, n = p - m * kArea;
             const int c = cls[p];
             float w = 0.f;
             if (c == 0) w = rho_tab[p];
             else if (c == 1) w = delta * rho_tab[p];
-            xt[p] = (w != 0.f) ? w * f[p] : 0.f;
-            wt[p] = w;
+            xt[m * kTileStride + n] = (w != 0.f) ? w * f[p] : 0.f;
+            wt[m * kTileStride + n] = w;
         }
     }
     __device__ void store(float gv) const { g[threadIdx.x] = gv; }
@@ -171,23 +177,36 @@ __device__ __forceinline__ void project_fp32(unsigned char *smem, const float2 *
     float2 *yw = reinterpret_cast<float2 *>(smem + kYwOff);
     const int tid = threadIdx.x;
 
-    constexpr int kOut = kArea * kHalfCols;  // 1584 per input
-    for (int o = tid; o < 2 * kOut; o += kThreads) {
-        const int which = o >= kOut;
-        const int rem = o - which * kOut;
-        const int m = rem / kHalfCols, kn = rem - m * kHalfCols;
-        const float *row = (which ? wt : xt) + m * kArea;
-        float re = 0.f, im = 0.f;
-        int t = 0;
-#pragma unroll 8
+    // Thread t < 192 owns row m of input t/48 % 2 and the columns
+    // k_n = t/96, t/96 + 2, ..., <= 32.  All lanes of a warp share k_n, so
+    // the twiddle reads are broadcasts, and they read 32 consecutive rows of
+    // one column (conflict-free with the 49-float row stride).
+    if (tid < 2 * 2 * kArea) {
+        const int p = tid % (2 * kArea), which = p / kArea, m = p - which * kArea;
+        const int kn0 = tid / (2 * kArea);
+        const float *row = (which ? wt : xt) + m * kTileStride;
+        constexpr int kCols = (kHalfCols + 1) / 2;  // 17
+        float re[kCols], im[kCols];
+#pragma unroll
+        for (int j = 0; j < kCols; ++j) re[j] = im[j] = 0.f;
         for (int n = 0; n < kArea; ++n) {
             const float v = row[n];
-            const float2 cs = tw[t];
-            re = fmaf(v, cs.x, re);
-            im = fmaf(-v, cs.y, im);
-            t = (t + kn) & (kDft - 1);
+#pragma unroll
+            for (int j = 0; j < kCols; ++j) {
+                const int kn = kn0 + 2 * j;
+                if (kn < kHalfCols) {
+                    const float2 cs = tw[(kn * n) & (kDft - 1)];
+                    re[j] = fmaf(v, cs.x, re[j]);
+                    im[j] = fmaf(-v, cs.y, im[j]);
+                }
+            }
         }
-        (which ? yw : yx)[m * kHalfCols + kn] = make_float2(re, im);
+        float2 *y = (which ? yw : yx) + m * kHalfCols;
+#pragma unroll
+        for (int j = 0; j < kCols; ++j) {
+            const int kn = kn0 + 2 * j;
+            if (kn < kHalfCols) y[kn] = make_float2(re[j], im[j]);
+        }
     }
     __syncthreads();
 
@@ -244,7 +263,7 @@ __device__ __forceinline__ float update_and_max(uint32_t wbase, u64 ndcr2, u64 d
         rre[r] = a;
         rim[r] = b;
         const float2 e = unpack2(energy2(a, b));
-        mx = fmaxf(mx, fmaxf(e.x, e.y));
+        mx = max3(mx, e.x, e.y);
     }
     return mx;
 }
@@ -297,47 +316,47 @@ __device__ __forceinline__ float run_block(const Src &src, const KParams &kp,
         const uint32_t wmx = __reduce_max_sync(0xffffffffu, __float_as_uint(tmx));
         if (l == 0) smax[w] = wmx;
         __syncthreads();
-        uint32_t estar = smax[0];
-#pragma unroll
-        for (int i = 1; i < kWarps; ++i) estar = max(estar, smax[i]);
+        // lanes 0..7 read the eight warp maxima in one access
+        const uint32_t estar =
+            __reduce_max_sync(0xffffffffu, l < kWarps ? smax[l] : 0u);
 
-        // Smallest linear index whose energy equals the maximum.
-        uint32_t kk = 0xffffffffu;
-        float cre = 0.f, cim = 0.f;
-        if (__float_as_uint(tmx) == estar) {
+        // Smallest linear index whose energy equals the maximum.  Only the
+        // warps that hold the maximum search (a warp-uniform branch).
+        if (__any_sync(0xffffffffu, __float_as_uint(tmx) == estar)) {
+            uint32_t kk = 0xffffffffu;
+            float cre = 0.f, cim = 0.f;
+            if (__float_as_uint(tmx) == estar) {
 #pragma unroll
-            for (int r = 7; r >= 0; --r) {
-                const float2 e = unpack2(energy2(rre[r], rim[r]));
-                const float2 re = unpack2(rre[r]), im = unpack2(rim[r]);
-                if (__float_as_uint(e.y) == estar) {
-                    kk = (uint32_t)((8 * w + r) * kDft + l + 32);
-                    cre = re.y;
-                    cim = im.y;
-                }
-                if (__float_as_uint(e.x) == estar) {
-                    kk = (uint32_t)((8 * w + r) * kDft + l);
-                    cre = re.x;
-                    cim = im.x;
+                for (int r = 7; r >= 0; --r) {
+                    const float2 e = unpack2(energy2(rre[r], rim[r]));
+                    const float2 re = unpack2(rre[r]), im = unpack2(rim[r]);
+                    if (__float_as_uint(e.y) == estar) {
+                        kk = (uint32_t)((8 * w + r) * kDft + l + 32);
+                        cre = re.y;
+                        cim = im.y;
+                    }
+                    if (__float_as_uint(e.x) == estar) {
+                        kk = (uint32_t)((8 * w + r) * kDft + l);
+                        cre = re.x;
+                        cim = im.x;
+                    }
                 }
             }
-        }
-        const uint32_t wk = __reduce_min_sync(0xffffffffu, kk);
-        const uint32_t bal = __ballot_sync(0xffffffffu, kk == wk && wk != 0xffffffffu);
-        if (bal) {
-            const int src_lane = __ffs(bal) - 1;
+            const uint32_t wk = __reduce_min_sync(0xffffffffu, kk);
+            const int src_lane = __ffs(__ballot_sync(0xffffffffu, kk == wk)) - 1;
             cre = __shfl_sync(0xffffffffu, cre, src_lane);
             cim = __shfl_sync(0xffffffffu, cim, src_lane);
+            if (l == 0) cand[w] = make_float4(__uint_as_float(wk), cre, cim, 0.f);
+        } else if (l == 0) {
+            cand[w].x = __uint_as_float(0xffffffffu);
         }
-        if (l == 0) cand[w] = make_float4(__uint_as_float(wk), cre, cim, 0.f);
         __syncthreads();
-        float4 best = cand[0];
-#pragma unroll
-        for (int i = 1; i < kWarps; ++i) {
-            const float4 c = cand[i];
-            if (__float_as_uint(c.x) < __float_as_uint(best.x)) best = c;
-        }
-        const uint32_t u = __float_as_uint(best.x);
-        const float dcr = best.y * gw, dci = best.z * gw;
+        // lanes 0..7 read the eight warp candidates; the smallest index wins
+        const float4 c = l < kWarps ? cand[l] : make_float4(__uint_as_float(0xffffffffu), 0.f, 0.f, 0.f);
+        const uint32_t u = __reduce_min_sync(0xffffffffu, __float_as_uint(c.x));
+        const int win = __ffs(__ballot_sync(0xffffffffu, __float_as_uint(c.x) == u)) - 1;
+        const float dcr = __shfl_sync(0xffffffffu, c.y, win) * gw;
+        const float dci = __shfl_sync(0xffffffffu, c.z, win) * gw;
         if (tid == 0) {
             dcl[it] = make_float2(dcr, dci);
             ul[it] = (uint16_t)u;
@@ -372,19 +391,40 @@ __device__ __forceinline__ float run_block(const Src &src, const KParams &kp,
         }
     }
 
-    // Eq. (1) on the centre block: Re sum_i dc_i exp(+j 2 pi (u_m m + u_n n)/64),
-    // compensated (Kahan) summation in FP32.
-    const int m = kBorder + (tid >> 4), n = kBorder + (tid & 15);
+    // Eq. (1) on the centre block: Re sum_it dc_it exp(+j 2 pi (u_m m + u_n n)/64)
+    // with m = 16 + i, n = 16 + j; the exponential factorises, so per chunk
+    // of iterations the tables P[it][i] = dc_it exp(+j 2 pi u_m m / 64) and
+    // E[it][j] = exp(+j 2 pi u_n n / 64) are built in the (now free) W4
+    // region.  Compensated (Kahan) summation in FP32.
+    const int si = tid >> 4, sj = tid & 15;
+    float2 *ptab = reinterpret_cast<float2 *>(smem);
+    float2 *etab = ptab + kSynChunk * 16;
     float s = 0.f, c = 0.f;
-    for (int it = 0; it < K; ++it) {
-        const float2 d = dcl[it];
-        const int u = ul[it];
-        const float2 cs = tw[((u >> 6) * m + (u & 63) * n) & (kDft - 1)];
-        const float term = fmaf(d.x, cs.x, -d.y * cs.y);
-        const float yv = term - c;
-        const float t = s + yv;
-        c = (t - s) - yv;
-        s = t;
+    for (int c0 = 0; c0 < K; c0 += kSynChunk) {
+        const int nc = min(kSynChunk, K - c0);
+        for (int e = tid; e < nc * 32; e += kThreads) {
+            const int it = e >> 5, q = e & 31;
+            const int u = ul[c0 + it];
+            if (q < 16) {
+                const float2 d = dcl[c0 + it];
+                const float2 cs = tw[((u >> 6) * (kBorder + q)) & (kDft - 1)];
+                ptab[it * 16 + q] =
+                    make_float2(fmaf(d.x, cs.x, -d.y * cs.y), fmaf(d.x, cs.y, d.y * cs.x));
+            } else {
+                etab[it * 16 + (q - 16)] = tw[((u & 63) * (kBorder + q - 16)) & (kDft - 1)];
+            }
+        }
+        __syncthreads();
+        for (int it = 0; it < nc; ++it) {
+            const float2 pv = ptab[it * 16 + si];
+            const float2 ev = etab[it * 16 + sj];
+            const float term = fmaf(pv.x, ev.x, -pv.y * ev.y);
+            const float yv = term - c;
+            const float t = s + yv;
+            c = (t - s) - yv;
+            s = t;
+        }
+        __syncthreads();
     }
     return s;
 }

@@ -181,11 +181,14 @@ void server_main(fse_ctx *ctx) {
                     ++it;
                 }
             }
+            int others = 0;
+            for (Slot &o : ctx->slots) others += (&o != &s) && o.busy;
             s.busy = true;
             const auto t0 = Clock::now();
             for (Request *r : s.reqs) {
                 r->t_start = t0;
                 r->stats.queue_ms = ms_between(r->t_submit, t0);
+                r->stats.inflight = others;
             }
             lk.unlock();
             int rc = launch_batch(ctx, s);

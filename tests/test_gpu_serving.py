@@ -46,21 +46,32 @@ def test_results_same_alone_and_in_the_mix(fse):
             out = np.empty_like(img)
             ctx.fse_conceal_batch_host([(img, mask, out)], params)
             alone.append(out)
-        ctx.fse_ctx_set_option(fse.FSE_OPT_SERVE_SLOTS, 3)
+        ctx.fse_ctx_set_option(fse.FSE_OPT_SERVE_SLOTS, 2)
         ctx.fse_ctx_set_option(fse.FSE_OPT_SERVE_MAX_BATCH, 4)
         outs = [np.full_like(img, 7) for img, _ in reqs]
         tickets = []
+        # a burst: requests arrive while earlier batches are on the GPU
         for i, (img, mask) in enumerate(reqs):
             t = ctx.fse_submit(img, mask, outs[i], params)
             assert t > 0
             tickets.append(t)
-            time.sleep(0.002)
         ctx.fse_drain(60000)
         stats = [ctx.fse_poll(t) for t in tickets]
         assert all(s is not None and s.status == 0 for s in stats)
         for i in range(len(reqs)):
             assert np.array_equal(outs[i], alone[i]), i
         assert max(s.batch_requests for s in stats) >= 2  # requests were batched
+        assert max(s.inflight for s in stats) >= 1        # batches overlapped
+        # and spaced arrivals: each is admitted as soon as a slot is free
+        outs2 = [np.empty_like(img) for img, _ in reqs[:4]]
+        t2 = []
+        for i, (img, mask) in enumerate(reqs[:4]):
+            t2.append(ctx.fse_submit(img, mask, outs2[i], params))
+            time.sleep(0.003)
+        ctx.fse_drain(60000)
+        for i, t in enumerate(t2):
+            assert ctx.fse_poll(t).status == 0
+            assert np.array_equal(outs2[i], alone[i])
         for s, (img, mask) in zip(stats, reqs):
             assert s.lost_blocks == int(
                 (np.add.reduceat(np.add.reduceat(mask, np.arange(0, mask.shape[0], 16), 0),
