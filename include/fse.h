@@ -50,6 +50,8 @@ extern "C" {
 #define FSE_ETIMEDOUT 4  /* a bounded device-side wait gave up              */
 #define FSE_ECUDA 5      /* a CUDA runtime call failed                      */
 #define FSE_ENOTFOUND 6  /* unknown ticket                                  */
+#define FSE_ETOOBIG 7    /* frame larger than fse_conceal_frame_noalloc's
+                            fixed scratch (1920 x 1088 samples)            */
 
 /* ---- parameters ---------------------------------------------------------- */
 #define FSE_ORDER_LINESCAN 0   /* conventional raster order, one block at a time */
@@ -209,6 +211,32 @@ int fse_copy_work(fse_ctx *ctx, int frame, float *dst, int dst_stride,
  * unspecified.  Only recorded while FSE_OPT_KEEP_TRACE is 1.
  * Errors: FSE_EINVAL for a bad index, NULL dst or no recorded trace. */
 int fse_copy_trace(fse_ctx *ctx, int frame, int16_t *dst, void *cuda_stream);
+
+/* Conceal one frame without allocating anything.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc, for example a plug-in whose host application owns all device
+ * memory through its own pool or budget, or code running where a stray
+ * allocation would break a memory plan fixed in advance.
+ *
+ * frame: luma, out and loss_mask are DEVICE pointers (as for
+ * fse_conceal_batch); at most 1920 x 1088 samples, else FSE_ETOOBIG.
+ * params: as for fse_conceal_batch; precision must be FSE_PREC_FP32; the
+ * executor field is ignored (one launch per processing-order group).
+ *
+ * Scratch: one fixed array of about 8.5 MB in device memory, declared in the
+ * library, that every GPU which loads the library holds until the process
+ * exits.  No context is needed and the call makes no device or host
+ * allocation (host staging is static too).  The first call on a device
+ * looks up that device's address of the array, so make it before any
+ * stream capture.  Every call shares the array: calls whose GPU work
+ * overlaps (other host threads, other streams) race and must be serialised
+ * by the caller; host-side staging is serialised internally.
+ * Stream-ordered on `cuda_stream`; the call synchronises that stream twice
+ * (to read the block-loss map and to release its staging) and returns with
+ * the extrapolation launches enqueued.
+ * Errors: FSE_EINVAL, FSE_ETOOBIG, FSE_ECUDA. */
+int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_params *params,
+                              void *cuda_stream);
 
 /* Context options (host-side settings; take effect on the next batch).
  *   FSE_OPT_SPIN_LIMIT       polls a device-side dependency wait makes

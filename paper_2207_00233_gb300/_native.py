@@ -15,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfse_gb300.so")
 
 FSE_OK, FSE_EINVAL, FSE_ENOMEM, FSE_EAGAIN, FSE_ETIMEDOUT, FSE_ECUDA, FSE_ENOTFOUND = range(7)
+FSE_ETOOBIG = 7
 FSE_ORDER_LINESCAN, FSE_ORDER_OPTIMIZED = 0, 1
 FSE_PREC_FP32, FSE_PREC_TF32, FSE_PREC_BF16, FSE_PREC_FP16, FSE_PREC_BF16X3 = range(5)
 FSE_EXEC_GROUPS, FSE_EXEC_PERSISTENT = 0, 1
@@ -23,7 +24,7 @@ FSE_MAX_ITERS = 1024
 EXPORTED = [
     "fse_plan_order", "fse_ctx_create", "fse_ctx_destroy", "fse_conceal_batch",
     "fse_conceal_batch_host", "fse_extrapolate_areas", "fse_submit", "fse_poll",
-    "fse_drain", "fse_last_batch_info", "fse_ctx_set_option", "fse_copy_work", "fse_copy_trace", "fse_last_kernel_ms", "fse_strerror",
+    "fse_drain", "fse_last_batch_info", "fse_ctx_set_option", "fse_copy_work", "fse_copy_trace", "fse_last_kernel_ms", "fse_conceal_frame_noalloc", "fse_strerror",
 ]
 FSE_OPT_SPIN_LIMIT, FSE_OPT_PERSISTENT_CTAS, FSE_OPT_SERVE_SLOTS = 1, 2, 3
 FSE_OPT_SERVE_MAX_BATCH, FSE_OPT_TEST_STUCK_DEP, FSE_OPT_KEEP_TRACE = 4, 5, 6
@@ -87,6 +88,7 @@ def lib() -> ctypes.CDLL:
     L.fse_copy_work.argtypes = [vp, cint, vp, cint, vp]
     L.fse_copy_trace.argtypes = [vp, cint, vp, vp]
     L.fse_last_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    L.fse_conceal_frame_noalloc.argtypes = [ctypes.POINTER(fse_frame), ctypes.POINTER(fse_params), vp]
     L.fse_strerror.argtypes = [cint]
     L.fse_strerror.restype = ctypes.c_char_p
     for name in EXPORTED:

@@ -734,6 +734,7 @@ extern "C" const char *fse_strerror(int status) {
     case FSE_ETIMEDOUT: return "a bounded device wait timed out";
     case FSE_ECUDA: return "CUDA runtime error";
     case FSE_ENOTFOUND: return "unknown ticket";
+    case FSE_ETOOBIG: return "frame larger than the fixed scratch of fse_conceal_frame_noalloc (1920 x 1088)";
     default: return "unknown status";
     }
 }
