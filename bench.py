@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--frames", type=int, default=FRAMES)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     return ap.parse_args()
 
 
@@ -117,6 +119,23 @@ class ClockSampler:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(value: float, device) -> float:
+    """The largest `value` over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(units_per_rank: int, steps: int, t_max_ms: float, world: int) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (every rank processes its own batch of the same size)."""
+    return world * units_per_rank * steps / (t_max_ms / 1e3)
 
 
 def make_workload(frames: int):
@@ -185,6 +204,112 @@ def cpu_baseline(frames):
                       f"OpenMP over the blocks of each group"}
 
 
+def precision_sweep(fse, ctx, dev):
+    """The 512x512 mixed-loss workload, K = 200, per projection dtype:
+    kernel blocks/s, and error against the FP64 oracle and the ground truth."""
+    import torch
+    import oracle
+    img, mask = fse_synth.workload_mixed_512()[0]
+    lost = mask == 1
+    o_work, _, _ = oracle.conceal_frame(img, mask, iters=K_ITERS, order=oracle.ORDER_OPTIMIZED,
+                                        threads=oracle.max_threads(), **PARAMS)
+    luma = torch.from_numpy(img).to(dev)
+    m = torch.from_numpy(mask).to(dev)
+    out = torch.empty_like(luma)
+    work = torch.empty(img.shape, dtype=torch.float32, device=dev)
+    gt = img[lost].astype(np.float64)
+
+    def psnr(a, b):
+        mse = float(np.mean((a - b) ** 2))
+        return float("inf") if mse == 0 else 10 * np.log10(255.0 ** 2 / mse)
+
+    res = {}
+    names = [("fp32", fse.FSE_PREC_FP32), ("tf32", fse.FSE_PREC_TF32),
+             ("bf16", fse.FSE_PREC_BF16), ("fp16", fse.FSE_PREC_FP16),
+             ("bf16x3", fse.FSE_PREC_BF16X3)]
+    for name, prec in names:
+        row = {}
+        for ex_name, ex in (("persistent", fse.FSE_EXEC_PERSISTENT), ("groups", fse.FSE_EXEC_GROUPS)):
+            p = fse.make_params(iters=K_ITERS, order=fse.FSE_ORDER_OPTIMIZED, executor=ex,
+                                precision=prec, **PARAMS)
+            ms = []
+            for _ in range(4):
+                ctx.fse_conceal_batch([(luma, m, out)], p)
+                ms.append(ctx.fse_last_kernel_ms())
+            blocks = ctx.fse_last_batch_info()["lost_blocks"]
+            row[f"blocks_per_s_{ex_name}"] = blocks / (min(ms[1:]) / 1e3)
+        ctx.fse_copy_work(0, work)
+        torch.cuda.synchronize()
+        g = work.cpu().numpy().astype(np.float64)[lost]
+        row.update({"max_abs_vs_oracle": float(np.abs(g - o_work[lost]).max()),
+                    "psnr_vs_oracle_db": psnr(g, o_work[lost]),
+                    "psnr_vs_truth_db": psnr(g, gt)})
+        res[name] = row
+    res["oracle_psnr_vs_truth_db"] = psnr(o_work[lost], gt)
+    res["workload"] = "512x512, 25% mixed isolated/burst block losses, K=200 (256 blocks)"
+    return res
+
+
+def serving_run(fse, rates=(50, 200, 1000), seconds=3.0, pool=12):
+    """Poisson arrivals of host-memory requests (frame sizes uniform over
+    352x288, 1280x720, 1920x1080, 3840x2160; 5-50% block losses, 20% with
+    full-row slices) through fse_submit / fse_poll."""
+    import time
+    reqs = [fse_synth.serving_request(i) for i in range(pool)]
+    params = fse.make_params(iters=K_ITERS, order=fse.FSE_ORDER_OPTIMIZED,
+                             executor=fse.FSE_EXEC_PERSISTENT, precision=fse.FSE_PREC_FP32,
+                             **PARAMS)
+    out = {}
+    rng = np.random.default_rng(7)
+    with fse.Context(0) as ctx:
+        ctx.fse_ctx_set_option(fse.FSE_OPT_SERVE_SLOTS, 4)
+        ctx.fse_ctx_set_option(fse.FSE_OPT_SERVE_MAX_BATCH, 16)
+        # warm-up
+        t = ctx.fse_submit(reqs[0][0], reqs[0][1], np.empty_like(reqs[0][0]), params)
+        ctx.fse_drain(60000)
+        ctx.fse_poll(t)
+        for rate in rates:
+            pending = {}
+            lat, blocks, refused, sub = [], 0, 0, 0
+            t0 = time.perf_counter()
+            next_t = t0
+            while True:
+                now = time.perf_counter()
+                if now - t0 >= seconds:
+                    break
+                if now >= next_t:
+                    img, mask = reqs[sub % pool]
+                    buf = np.empty_like(img)
+                    tk = ctx.fse_submit(img, mask, buf, params)
+                    if tk < 0:
+                        refused += 1
+                    else:
+                        pending[tk] = buf
+                    sub += 1
+                    next_t += rng.exponential(1.0 / rate)
+                for tk in list(pending):
+                    st = ctx.fse_poll(tk)
+                    if st is not None:
+                        lat.append(st.latency_ms)
+                        blocks += st.lost_blocks
+                        del pending[tk]
+                time.sleep(0.0002)
+            ctx.fse_drain(600000)
+            t_end = time.perf_counter()
+            for tk in list(pending):
+                st = ctx.fse_poll(tk)
+                lat.append(st.latency_ms)
+                blocks += st.lost_blocks
+            lat = np.array(lat)
+            out[str(rate)] = {"submitted": sub, "refused": refused, "completed": int(lat.size),
+                              "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
+                              "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
+                              "blocks_per_s": blocks / (t_end - t0)}
+    out["setup"] = (f"{seconds:.0f} s of Poisson arrivals per rate (req/s), {pool} distinct "
+                    "requests cycled, 4 device slots, up to 16 requests per batch, K=200, fp32")
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -243,12 +368,8 @@ def main():
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_ms = float(np.sum(step_ms))
-    t_max = t_ms
-    if world > 1:
-        t = torch.tensor([t_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * lost_blocks * args.steps / (t_max / 1e3)
+    t_max = max_over_ranks(t_ms, dev)
+    value = weak_scaling_value(lost_blocks, args.steps, t_max, world)
 
     # ---- end to end through the host-buffer entry point ----
     pinned = []
@@ -308,6 +429,12 @@ def main():
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(frames)
+    sweep = None
+    if rank == 0 and not args.no_sweep:
+        sweep = precision_sweep(fse, ctx, dev)
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        serving = serving_run(fse)
 
     if rank == 0:
         line = {
@@ -333,6 +460,10 @@ def main():
         }
         if base is not None:
             line["cpu_baseline"] = base
+        if sweep is not None:
+            line["precision_sweep"] = sweep
+        if serving is not None:
+            line["serving"] = serving
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

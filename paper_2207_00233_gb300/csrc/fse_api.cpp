@@ -144,6 +144,39 @@ const float *fse_ctx::rho_table(float rho, int *rc) {
     return static_cast<const float *>(b.ptr);
 }
 
+const uint4 *fse_ctx::frag_table(int precision, int *rc) {
+    *rc = FSE_OK;
+    if (precision == FSE_PREC_FP32) return nullptr;
+    if (precision < 0 || precision > 4) {
+        *rc = FSE_EINVAL;
+        return nullptr;
+    }
+    {
+        std::lock_guard<std::mutex> lk(mem_mu);
+        if (frags[precision].ptr) return static_cast<const uint4 *>(frags[precision].ptr);
+    }
+    DevBuf b;
+    *rc = dev_reserve(b, frag_bytes(precision));
+    if (*rc) return nullptr;
+    if (launch_build_frags(precision, static_cast<const float2 *>(tw_dev.ptr),
+                           static_cast<uint4 *>(b.ptr), nullptr) != cudaSuccess ||
+        cudaStreamSynchronize(nullptr) != cudaSuccess) {
+        cudaGetLastError();
+        dev_release(b);
+        *rc = FSE_ECUDA;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(mem_mu);
+    if (frags[precision].ptr) {  // built concurrently by another thread
+        DevBuf extra = b;
+        used -= extra.cap;
+        cudaFree(extra.ptr);
+        return static_cast<const uint4 *>(frags[precision].ptr);
+    }
+    frags[precision] = b;
+    return static_cast<const uint4 *>(b.ptr);
+}
+
 // ---------------------------------------------------------------------------
 // Validation
 // ---------------------------------------------------------------------------
@@ -186,6 +219,8 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
     int rc = FSE_OK;
     const float *rho_tab = ctx->rho_table(p->rho, &rc);
     if (!rho_tab) return rc;
+    const uint4 *frags = ctx->frag_table(p->precision, &rc);
+    if (rc) return rc;
     // The staging buffers of the previous batch on this workspace must have
     // been consumed before they are overwritten.
     if (ws.staged) {
@@ -409,7 +444,7 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
     }
 
     // ---- extrapolation ----
-    const KParams kp{p->rho, p->delta, p->gamma, p->iters};
+    const KParams kp{p->rho, p->delta, p->gamma, p->iters, frags};
     const FrameDesc *fdev = static_cast<const FrameDesc *>(ws.frames.ptr);
     const float2 *tw_tab = static_cast<const float2 *>(ctx->tw_dev.ptr);
     int launches = 1;  // block-loss map
@@ -558,6 +593,7 @@ extern "C" void fse_ctx_destroy(fse_ctx *ctx) {
     release_workspace(ctx, ctx->ws);
     ctx->dev_release(ctx->tw_dev);
     for (auto &e : ctx->rho_tabs) ctx->dev_release(e.second);
+    for (auto &f : ctx->frags) ctx->dev_release(f);
     delete ctx;
 }
 
@@ -636,7 +672,9 @@ extern "C" int fse_extrapolate_areas(fse_ctx *ctx, const float *area_f,
     cudaSetDevice(ctx->device);
     const float *rho_tab = ctx->rho_table(params->rho, &rc);
     if (!rho_tab) return rc;
-    const KParams kp{params->rho, params->delta, params->gamma, params->iters};
+    const uint4 *frags = ctx->frag_table(params->precision, &rc);
+    if (rc) return rc;
+    const KParams kp{params->rho, params->delta, params->gamma, params->iters, frags};
     CK(launch_areas(area_f, area_cls, n, kp, rho_tab,
                     static_cast<const float2 *>(ctx->tw_dev.ptr), params->precision, g_out,
                     u_out, dc_out, r_out, static_cast<cudaStream_t>(cuda_stream)));

@@ -54,7 +54,24 @@ static_assert(kSynChunk * 32 * 8 <= kW4Bytes, "synthesis tables overflow");
 struct KParams {
     float rho, delta, gamma;
     int iters;
+    const uint4 *frags;  // packed DFT operand fragments of the tensor-core
+                         // projection (null for FSE_PREC_FP32)
 };
+
+// Tensor-core projection (warp-level mma.sync).  Stage 1 multiplies the
+// stacked area tiles [w*f; w] (96 x 48) by [cos | -sin] (48 x 80, half
+// spectrum k_n = 0..32, padded to 40 columns each); stage 2 multiplies
+// [cos | sin](k_m) (64 x 96) by [[Y_re, Y_im]; [Y_im, -Y_re]] (96 x 80 per
+// input), which gives Re and Im of the spectrum directly.
+constexpr int kYRows = 2 * kArea;           // 96
+constexpr int kYCols = 80;                  // 40 real + 40 imaginary
+constexpr int kYStride = kYCols + 4;        // conflict-free fragment loads
+constexpr int kYOff = 2 * kArea * kTileStride * 4;                 // after the tiles
+constexpr int kR0Off = kYOff + kYRows * kYStride * 4;              // 64 x 33 float2
+static_assert(kR0Off + kDft * kHalfCols * 8 <= kW4Bytes, "projection scratch overflow");
+size_t frag_bytes(int precision);
+cudaError_t launch_build_frags(int precision, const float2 *tw, uint4 *out,
+                               cudaStream_t stream);
 
 // Device-side description of one frame of a batch.
 struct FrameDesc {

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "../../include/fse.h"
 #include "fse_internal.h"
@@ -228,6 +229,305 @@ __device__ __forceinline__ void project_fp32(unsigned char *smem, const float2 *
     stage2_rows(yw, tw, w, l, wre, wim);
 }
 
+// ---- projection on the tensor cores (warp-level mma.sync) --------------------
+
+__device__ __forceinline__ uint32_t pk_bf16(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+__device__ __forceinline__ uint32_t pk_f16(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+__device__ __forceinline__ uint32_t cv_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+// The two floats a bf16x2 register holds (exact).
+__device__ __forceinline__ float bf_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void mma_f16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                        uint32_t a3, uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
+                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
+                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Per precision: K per mma instruction, and the operand registers of one
+// fragment (x3 precisions carry a low part as well).
+template <int P> struct Prec {
+    static constexpr int kStep = (P == FSE_PREC_TF32) ? 8 : 16;
+    static constexpr bool kSplit = (P == FSE_PREC_BF16X3);
+};
+
+// An operand fragment: the 4 (A) or 2 (B) registers, plus the low parts.
+struct FragA { uint32_t h[4], l[4]; };
+struct FragB { uint32_t h[2], l[2]; };
+
+// Pack two values that share a register, in the precision's type.
+template <int P>
+__device__ __forceinline__ void pack_pair(float v0, float v1, uint32_t &h, uint32_t &l) {
+    if (P == FSE_PREC_FP16) {
+        h = pk_f16(v0, v1);
+    } else {
+        h = pk_bf16(v0, v1);
+        if (P == FSE_PREC_BF16X3) l = pk_bf16(v0 - bf_lo(h), v1 - bf_hi(h));
+    }
+}
+
+// Fragment of a row-major A (16 x kStep) starting at (r0, k0) from a value
+// functor A(row, k): the m16n8k16 / m16n8k8 register layouts.
+template <int P, class FA>
+__device__ __forceinline__ FragA load_a(FA A, int r0, int k0) {
+    const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
+    FragA f;
+    if (P == FSE_PREC_TF32) {
+        f.h[0] = cv_tf32(A(r0 + g, k0 + t));
+        f.h[1] = cv_tf32(A(r0 + g + 8, k0 + t));
+        f.h[2] = cv_tf32(A(r0 + g, k0 + t + 4));
+        f.h[3] = cv_tf32(A(r0 + g + 8, k0 + t + 4));
+    } else {
+        pack_pair<P>(A(r0 + g, k0 + 2 * t), A(r0 + g, k0 + 2 * t + 1), f.h[0], f.l[0]);
+        pack_pair<P>(A(r0 + g + 8, k0 + 2 * t), A(r0 + g + 8, k0 + 2 * t + 1), f.h[1], f.l[1]);
+        pack_pair<P>(A(r0 + g, k0 + 2 * t + 8), A(r0 + g, k0 + 2 * t + 9), f.h[2], f.l[2]);
+        pack_pair<P>(A(r0 + g + 8, k0 + 2 * t + 8), A(r0 + g + 8, k0 + 2 * t + 9), f.h[3],
+                     f.l[3]);
+    }
+    return f;
+}
+
+// Fragment of a (kStep x 8) B starting at (k0, c0) from a functor B(k, col).
+template <int P, class FB>
+__device__ __forceinline__ FragB load_b(FB B, int k0, int c0) {
+    const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
+    FragB f;
+    if (P == FSE_PREC_TF32) {
+        f.h[0] = cv_tf32(B(k0 + t, c0 + g));
+        f.h[1] = cv_tf32(B(k0 + t + 4, c0 + g));
+    } else {
+        pack_pair<P>(B(k0 + 2 * t, c0 + g), B(k0 + 2 * t + 1, c0 + g), f.h[0], f.l[0]);
+        pack_pair<P>(B(k0 + 2 * t + 8, c0 + g), B(k0 + 2 * t + 9, c0 + g), f.h[1], f.l[1]);
+    }
+    return f;
+}
+
+template <int P>
+__device__ __forceinline__ void mma_step(float (&d)[4], const FragA &a, const FragB &b) {
+    if (P == FSE_PREC_TF32) {
+        mma_tf32(d, a.h[0], a.h[1], a.h[2], a.h[3], b.h[0], b.h[1]);
+    } else if (P == FSE_PREC_FP16) {
+        mma_f16(d, a.h[0], a.h[1], a.h[2], a.h[3], b.h[0], b.h[1]);
+    } else {
+        mma_bf16(d, a.h[0], a.h[1], a.h[2], a.h[3], b.h[0], b.h[1]);
+        if (P == FSE_PREC_BF16X3) {
+            mma_bf16(d, a.h[0], a.h[1], a.h[2], a.h[3], b.l[0], b.l[1]);
+            mma_bf16(d, a.l[0], a.l[1], a.l[2], a.l[3], b.h[0], b.h[1]);
+        }
+    }
+}
+
+// The constant operands: stage-1 B = [cos | -sin](k_n, n) and stage-2
+// A = [cos | sin](k_m, m), from the exactly symmetric twiddle table.
+struct DftB1 {
+    const float2 *tw;
+    __device__ float operator()(int k, int c) const {
+        const int kn = c < 40 ? c : c - 40;
+        if (kn >= kHalfCols) return 0.f;
+        const float2 cs = tw[(kn * k) & (kDft - 1)];
+        return c < 40 ? cs.x : -cs.y;
+    }
+};
+struct DftA2 {
+    const float2 *tw;
+    __device__ float operator()(int km, int k) const {
+        const float2 cs = tw[(km * (k < kArea ? k : k - kArea)) & (kDft - 1)];
+        return k < kArea ? cs.x : cs.y;
+    }
+};
+
+// Packed fragments of the constant operands, per precision:
+//   stage-1 B: [10 n-tiles][K/kStep][32 lanes] -> uint4 (h0, h1, l0, l1)
+//   stage-2 A: [4 m-tiles][96/kStep][32 lanes] -> 2 x uint4 (h0..h3, l0..l3)
+template <int P> struct FragLayout {
+    static constexpr int kS1 = kArea / Prec<P>::kStep;
+    static constexpr int kS2 = 2 * kArea / Prec<P>::kStep;
+    static constexpr int kB1 = 10 * kS1 * 32;       // uint4 entries
+    static constexpr int kA2 = 4 * kS2 * 32 * 2;    // uint4 entries
+};
+
+template <int P>
+__global__ void k_build_frags(const float2 *tw, uint4 *out) {
+    using L = FragLayout<P>;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;  // one warp per fragment
+    const int frag = i >> 5;
+    if (frag < 10 * L::kS1) {
+        const int nt = frag / L::kS1, ks = frag % L::kS1;
+        const FragB f = load_b<P>(DftB1{tw}, ks * Prec<P>::kStep, nt * 8);
+        out[i] = make_uint4(f.h[0], f.h[1], Prec<P>::kSplit ? f.l[0] : 0u,
+                            Prec<P>::kSplit ? f.l[1] : 0u);
+    } else if (frag < 10 * L::kS1 + 4 * L::kS2) {
+        const int j = frag - 10 * L::kS1;
+        const int mt = j / L::kS2, ks = j % L::kS2;
+        const FragA f = load_a<P>(DftA2{tw}, mt * 16, ks * Prec<P>::kStep);
+        const int base = L::kB1 + (j * 32 + (i & 31)) * 2;
+        out[base] = make_uint4(f.h[0], f.h[1], f.h[2], f.h[3]);
+        out[base + 1] = Prec<P>::kSplit ? make_uint4(f.l[0], f.l[1], f.l[2], f.l[3])
+                                        : make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// Data operands: stage-1 A = the stacked tiles, stage-2 B from Y.
+struct TileA1 {
+    const float *xt, *wt;
+    __device__ float operator()(int r, int k) const {
+        return r < kArea ? xt[r * kTileStride + k] : wt[(r - kArea) * kTileStride + k];
+    }
+};
+struct YB2 {
+    const float *y;  // rows of this input's Y
+    __device__ float operator()(int k, int c) const {
+        if (k < kArea) return y[k * kYStride + c];
+        const float *row = y + (k - kArea) * kYStride;
+        return c < 40 ? row[c + 40] : -row[c - 40];
+    }
+};
+
+template <int P>
+__device__ __forceinline__ void project_mma(unsigned char *smem, const uint4 *frags,
+                                            u64 (&rre)[8], u64 (&rim)[8],
+                                            float (&wacc)[5][4]) {
+    using L = FragLayout<P>;
+    constexpr int KS = Prec<P>::kStep;
+    const float *xt = reinterpret_cast<const float *>(smem + kXTileOff);
+    const float *wt = reinterpret_cast<const float *>(smem + kWTileOff);
+    float *y = reinterpret_cast<float *>(smem + kYOff);
+    float2 *r0h = reinterpret_cast<float2 *>(smem + kR0Off);
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+
+    // Stage 1: Y (96 x 80) = tiles (96 x 48) x B1 (48 x 80); 6 x 10 tiles.
+    for (int tile = w; tile < 60; tile += kWarps) {
+        const int mt = tile / 10, nt = tile % 10;
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int ks = 0; ks < L::kS1; ++ks) {
+            const FragA a = load_a<P>(TileA1{xt, wt}, mt * 16, ks * KS);
+            const uint4 bv = frags[(nt * L::kS1 + ks) * 32 + lane];
+            FragB b;
+            b.h[0] = bv.x; b.h[1] = bv.y; b.l[0] = bv.z; b.l[1] = bv.w;
+            mma_step<P>(d, a, b);
+        }
+        float *y0 = y + (mt * 16 + g) * kYStride + nt * 8 + 2 * t;
+        y0[0] = d[0];
+        y0[1] = d[1];
+        y0[8 * kYStride] = d[2];
+        y0[8 * kYStride + 1] = d[3];
+    }
+    __syncthreads();
+
+    // Stage 2: warp w takes m-tile w & 3 and the n-tiles (w >> 2) * 5 .. +5 of
+    // both inputs (x: R_w, then w: W).
+    const int mt = w & 3, nt0 = (w >> 2) * 5;
+    float xacc[5][4];
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) xacc[j][q] = wacc[j][q] = 0.f;
+#pragma unroll 1
+    for (int ks = 0; ks < L::kS2; ++ks) {
+        const int fi = L::kB1 + ((mt * L::kS2 + ks) * 32 + lane) * 2;
+        const uint4 ah = frags[fi], al = frags[fi + 1];
+        FragA a;
+        a.h[0] = ah.x; a.h[1] = ah.y; a.h[2] = ah.z; a.h[3] = ah.w;
+        a.l[0] = al.x; a.l[1] = al.y; a.l[2] = al.z; a.l[3] = al.w;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            mma_step<P>(xacc[j], a, load_b<P>(YB2{y}, ks * KS, (nt0 + j) * 8));
+            mma_step<P>(wacc[j], a, load_b<P>(YB2{y + kArea * kYStride}, ks * KS, (nt0 + j) * 8));
+        }
+    }
+    // R_w, half spectrum, into the staging area (R0h[k_m][k_n], k_n <= 32).
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int km = mt * 16 + g + (q >> 1) * 8;
+            const int c = (nt0 + j) * 8 + 2 * t + (q & 1);
+            if (c < kHalfCols) r0h[km * kHalfCols + c].x = xacc[j][q];
+            else if (c >= 40 && c < 40 + kHalfCols) r0h[km * kHalfCols + c - 40].y = xacc[j][q];
+        }
+    __syncthreads();
+    // The entries this thread owns; k_n > 32 from the conjugate mirror.
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int km = 8 * w + r;
+        const float2 a = r0h[km * kHalfCols + lane];
+        float2 b;
+        if (lane == 0) {
+            b = r0h[km * kHalfCols + 32];
+        } else {
+            b = r0h[((kDft - km) & (kDft - 1)) * kHalfCols + 32 - lane];
+            b.y = -b.y;
+        }
+        rre[r] = pack2(a.x, b.x);
+        rim[r] = pack2(a.y, b.y);
+    }
+}
+
+// W from the stage-2 fragments into the W4 layout (direct and conjugate
+// mirror entries, repeated rows); the weight sum W[0] into *w0.
+__device__ __forceinline__ void store_w4_frags(unsigned char *smem, const float (&wacc)[5][4],
+                                               float *w0) {
+    float *w4 = reinterpret_cast<float *>(smem);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int mt = w & 3, nt0 = (w >> 2) * 5;
+    auto put = [&](int row, int col, int comp, float v) {
+        // comp 0: real, 1: imaginary; slot .x/.z as the first member of
+        // W4[row][col], .y/.w as the second member of W4[row][col ^ 32]
+        const int a = (row * kDft + col) * 4 + 2 * comp;
+        const int b = (row * kDft + (col ^ 32)) * 4 + 2 * comp + 1;
+        w4[a] = v;
+        w4[b] = v;
+        if (row < kW4Rows - kDft) {
+            w4[a + kDft * kDft * 4] = v;
+            w4[b + kDft * kDft * 4] = v;
+        }
+    };
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int km = mt * 16 + g + (q >> 1) * 8;
+            const int c = (nt0 + j) * 8 + 2 * t + (q & 1);
+            const int comp = c < 40 ? 0 : 1;
+            const int kn = c < 40 ? c : c - 40;
+            if (kn >= kHalfCols) continue;
+            const float v = wacc[j][q];
+            put(km, kn, comp, v);
+            if (kn != 0 && kn != 32)
+                put((kDft - km) & (kDft - 1), kDft - kn, comp, comp ? -v : v);
+            if (km == 0 && c == 0) *w0 = v;
+        }
+}
+
 // Store the thread's W entries in the W4 layout (plus the repeated rows).
 __device__ __forceinline__ void store_w4(unsigned char *smem, const float (&wre)[8][2],
                                          const float (&wim)[8][2]) {
@@ -277,7 +577,7 @@ __device__ __forceinline__ uint32_t w4_base(uint32_t w4addr, int um, int un) {
 
 // The full per-block computation.  Returns the model value of this thread's
 // sample of the centre block (unclamped).
-template <bool kTrace, class Src>
+template <int P, bool kTrace, class Src>
 __device__ __forceinline__ float run_block(const Src &src, const KParams &kp,
                                            const float *rho_tab, const float2 *tw_g,
                                            unsigned char *smem, const Trace &tr) {
@@ -295,12 +595,17 @@ __device__ __forceinline__ float run_block(const Src &src, const KParams &kp,
     __syncthreads();
 
     u64 rre[8], rim[8];
-    {
+    if (P == FSE_PREC_FP32) {
         float wre[8][2], wim[8][2];
         project_fp32(smem, tw, rre, rim, wre, wim);
         __syncthreads();  // all reads of the stage-1 scratch are done
         store_w4(smem, wre, wim);
         if (tid == 0) misc[0] = wre[0][0];  // W[0] = sum of the weights
+    } else {
+        float wacc[5][4];
+        project_mma<P>(smem, kp.frags, rre, rim, wacc);
+        __syncthreads();  // all reads of the projection scratch are done
+        store_w4_frags(smem, wacc, misc);
     }
     __syncthreads();
 
@@ -444,6 +749,7 @@ __device__ __forceinline__ void write_frame_trace(const FrameDesc &fd, int block
         t[it] = (W0 > 0.f) ? (int16_t)ul[it] : (int16_t)-1;
 }
 
+template <int P>
 __global__ void __launch_bounds__(kThreads, 3)
 k_group(const FrameDesc *frames, const int2 *items, KParams kp, const float *rho_tab,
         const float2 *tw_tab) {
@@ -451,7 +757,7 @@ k_group(const FrameDesc *frames, const int2 *items, KParams kp, const float *rho
     const int2 item = items[blockIdx.x];
     const FrameDesc &fd = frames[item.x];
     const FrameSrc src(fd, item.y);
-    const float g = run_block<false>(src, kp, rho_tab, tw_tab, smem, Trace{nullptr, nullptr, nullptr});
+    const float g = run_block<P, false>(src, kp, rho_tab, tw_tab, smem, Trace{nullptr, nullptr, nullptr});
     src.store(g);
     write_frame_trace(fd, item.y, kp, smem);
 }
@@ -462,6 +768,7 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
     return v;
 }
 
+template <int P>
 __global__ void __launch_bounds__(kThreads, 3)
 k_persistent(const FrameDesc *frames, DepGraph dg, KParams kp, const float *rho_tab,
              const float2 *tw_tab) {
@@ -495,7 +802,7 @@ k_persistent(const FrameDesc *frames, DepGraph dg, KParams kp, const float *rho_
         const int2 item = dg.items[i];
         const FrameDesc &fd = frames[item.x];
         const FrameSrc src(fd, item.y);
-        const float g = run_block<false>(src, kp, rho_tab, tw_tab, smem, Trace{nullptr, nullptr, nullptr});
+        const float g = run_block<P, false>(src, kp, rho_tab, tw_tab, smem, Trace{nullptr, nullptr, nullptr});
         src.store(g);
         write_frame_trace(fd, item.y, kp, smem);
         __threadfence();
@@ -507,6 +814,7 @@ k_persistent(const FrameDesc *frames, DepGraph dg, KParams kp, const float *rho_
     }
 }
 
+template <int P>
 __global__ void __launch_bounds__(kThreads, 3)
 k_areas(const float *area_f, const uint8_t *area_cls, KParams kp, const float *rho_tab,
         const float2 *tw_tab, float *g_out, int32_t *u_out, float *dc_out, float *r_out) {
@@ -517,7 +825,7 @@ k_areas(const float *area_f, const uint8_t *area_cls, KParams kp, const float *r
     const Trace tr{u_out ? u_out + a * kp.iters : nullptr,
                    dc_out ? dc_out + a * kp.iters * 2 : nullptr,
                    r_out ? r_out + a * kDft * kDft * 2 : nullptr};
-    const float g = run_block<true>(src, kp, rho_tab, tw_tab, smem, tr);
+    const float g = run_block<P, true>(src, kp, rho_tab, tw_tab, smem, tr);
     src.store(g);
 }
 
@@ -539,28 +847,67 @@ __global__ void k_block_loss(const FrameDesc *frames, uint8_t *lost, const int *
 
 // ---- launchers ------------------------------------------------------------------
 
-static bool g_attr_done = false;
-
-static cudaError_t ensure_attrs() {
-    if (g_attr_done) return cudaSuccess;
-    const int max_smem = smem_bytes(FSE_MAX_ITERS);
-    cudaError_t e;
-    e = cudaFuncSetAttribute(k_group, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_areas, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-    if (e != cudaSuccess) return e;
-    g_attr_done = true;
-    return cudaSuccess;
+// Calls f with the precision as a compile-time constant.
+template <class F>
+static cudaError_t with_precision(int precision, F f) {
+    switch (precision) {
+    case FSE_PREC_FP32: return f(std::integral_constant<int, FSE_PREC_FP32>());
+    case FSE_PREC_TF32: return f(std::integral_constant<int, FSE_PREC_TF32>());
+    case FSE_PREC_BF16: return f(std::integral_constant<int, FSE_PREC_BF16>());
+    case FSE_PREC_FP16: return f(std::integral_constant<int, FSE_PREC_FP16>());
+    case FSE_PREC_BF16X3: return f(std::integral_constant<int, FSE_PREC_BF16X3>());
+    default: return cudaErrorInvalidValue;
+    }
 }
 
-bool precision_supported(int precision) { return precision == FSE_PREC_FP32; }
+static bool g_attr_done[5] = {false, false, false, false, false};
+
+static cudaError_t ensure_attrs(int precision) {
+    if (precision < 0 || precision > 4) return cudaErrorInvalidValue;
+    if (g_attr_done[precision]) return cudaSuccess;
+    const int max_smem = smem_bytes(FSE_MAX_ITERS);
+    cudaError_t e = with_precision(precision, [&](auto pc) {
+        constexpr int P = decltype(pc)::value;
+        cudaError_t r = cudaFuncSetAttribute(k_group<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             max_smem);
+        if (r != cudaSuccess) return r;
+        r = cudaFuncSetAttribute(k_persistent<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 max_smem);
+        if (r != cudaSuccess) return r;
+        return cudaFuncSetAttribute(k_areas<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    max_smem);
+    });
+    if (e == cudaSuccess) g_attr_done[precision] = true;
+    return e;
+}
+
+bool precision_supported(int precision) { return precision >= 0 && precision <= 4; }
+
+size_t frag_bytes(int precision) {
+    size_t n = 0;
+    with_precision(precision, [&](auto pc) {
+        constexpr int P = decltype(pc)::value;
+        n = (size_t)(FragLayout<P>::kB1 + FragLayout<P>::kA2) * sizeof(uint4);
+        return cudaSuccess;
+    });
+    return precision == FSE_PREC_FP32 ? 0 : n;
+}
+
+cudaError_t launch_build_frags(int precision, const float2 *tw, uint4 *out, cudaStream_t stream) {
+    if (precision == FSE_PREC_FP32) return cudaSuccess;
+    return with_precision(precision, [&](auto pc) {
+        constexpr int P = decltype(pc)::value;
+        using L = FragLayout<P>;
+        const int warps = 10 * L::kS1 + 4 * L::kS2;
+        k_build_frags<P><<<(warps * 32 + 255) / 256, 256, 0, stream>>>(tw, out);
+        return cudaGetLastError();
+    });
+}
 
 int max_resident_ctas(int iters) {
-    if (ensure_attrs() != cudaSuccess) return 1;
+    if (ensure_attrs(FSE_PREC_FP32) != cudaSuccess) return 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent, kThreads,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent<FSE_PREC_FP32>, kThreads,
                                                       smem_bytes(iters)) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
@@ -583,24 +930,32 @@ cudaError_t launch_group(const FrameDesc *frames_dev, const int2 *items, int n_i
                          const KParams &kp, const float *rho_tab, const float2 *tw_tab,
                          int precision, cudaStream_t stream) {
     if (!precision_supported(precision)) return cudaErrorInvalidValue;
-    cudaError_t e = ensure_attrs();
+    if (precision != FSE_PREC_FP32 && !kp.frags) return cudaErrorInvalidValue;
+    cudaError_t e = ensure_attrs(precision);
     if (e != cudaSuccess) return e;
     if (n_items <= 0) return cudaSuccess;
-    k_group<<<n_items, kThreads, smem_bytes(kp.iters), stream>>>(frames_dev, items, kp,
-                                                                 rho_tab, tw_tab);
-    return cudaGetLastError();
+    return with_precision(precision, [&](auto pc) {
+        constexpr int P = decltype(pc)::value;
+        k_group<P><<<n_items, kThreads, smem_bytes(kp.iters), stream>>>(frames_dev, items, kp,
+                                                                        rho_tab, tw_tab);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_persistent(const FrameDesc *frames_dev, const DepGraph &dg,
                               const KParams &kp, const float *rho_tab, const float2 *tw_tab,
                               int precision, int grid, cudaStream_t stream) {
     if (!precision_supported(precision)) return cudaErrorInvalidValue;
-    cudaError_t e = ensure_attrs();
+    if (precision != FSE_PREC_FP32 && !kp.frags) return cudaErrorInvalidValue;
+    cudaError_t e = ensure_attrs(precision);
     if (e != cudaSuccess) return e;
     if (dg.n <= 0) return cudaSuccess;
-    k_persistent<<<grid, kThreads, smem_bytes(kp.iters), stream>>>(frames_dev, dg, kp,
-                                                                   rho_tab, tw_tab);
-    return cudaGetLastError();
+    return with_precision(precision, [&](auto pc) {
+        constexpr int P = decltype(pc)::value;
+        k_persistent<P><<<grid, kThreads, smem_bytes(kp.iters), stream>>>(frames_dev, dg, kp,
+                                                                          rho_tab, tw_tab);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_areas(const float *area_f, const uint8_t *area_cls, int n,
@@ -608,12 +963,16 @@ cudaError_t launch_areas(const float *area_f, const uint8_t *area_cls, int n,
                          int precision, float *g_out, int32_t *u_out, float *dc_out,
                          float *r_out, cudaStream_t stream) {
     if (!precision_supported(precision)) return cudaErrorInvalidValue;
-    cudaError_t e = ensure_attrs();
+    if (precision != FSE_PREC_FP32 && !kp.frags) return cudaErrorInvalidValue;
+    cudaError_t e = ensure_attrs(precision);
     if (e != cudaSuccess) return e;
     if (n <= 0) return cudaSuccess;
-    k_areas<<<n, kThreads, smem_bytes(kp.iters), stream>>>(area_f, area_cls, kp, rho_tab,
-                                                           tw_tab, g_out, u_out, dc_out, r_out);
-    return cudaGetLastError();
+    return with_precision(precision, [&](auto pc) {
+        constexpr int P = decltype(pc)::value;
+        k_areas<P><<<n, kThreads, smem_bytes(kp.iters), stream>>>(
+            area_f, area_cls, kp, rho_tab, tw_tab, g_out, u_out, dc_out, r_out);
+        return cudaGetLastError();
+    });
 }
 
 }  // namespace fse

@@ -268,7 +268,7 @@ extern "C" int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_param
     if (frame->out != frame->luma)
         NA_CK(cudaMemcpy2DAsync(frame->out, frame->stride, frame->luma, frame->stride, W, H,
                                 cudaMemcpyDeviceToDevice, stream));
-    const KParams kp{params->rho, params->delta, params->gamma, params->iters};
+    const KParams kp{params->rho, params->delta, params->gamma, params->iters, nullptr};
     for (int g = 0; g < n_groups; ++g)
         NA_CK(launch_group(d_desc, d_items + h_group_start[g],
                            h_group_start[g + 1] - h_group_start[g], kp, d_rho, d_tw,
