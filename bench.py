@@ -264,8 +264,9 @@ def serving_run(fse, rates=(50, 200, 1000), seconds=3.0, pool=12):
     with fse.Context(0) as ctx:
         ctx.fse_ctx_set_option(fse.FSE_OPT_SERVE_SLOTS, 4)
         ctx.fse_ctx_set_option(fse.FSE_OPT_SERVE_MAX_BATCH, 16)
-        # warm-up
-        t = ctx.fse_submit(reqs[0][0], reqs[0][1], np.empty_like(reqs[0][0]), params)
+        # warm-up (the output buffer is borrowed until the request is done)
+        warm_out = np.empty_like(reqs[0][0])
+        t = ctx.fse_submit(reqs[0][0], reqs[0][1], warm_out, params)
         ctx.fse_drain(60000)
         ctx.fse_poll(t)
         for rate in rates:
