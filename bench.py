@@ -42,6 +42,9 @@ FLOP_PER_ITER = 4096 * 11  # complex multiply-subtract (8) + |R|^2 (3)
 SMS = 152
 SMEM_BYTES_PER_CLK = 128
 FP32_LANES = 128
+# DRAM bytes (read + write) of one k_persistent<FP32> launch on this workload,
+# from the ncu capture summarised in profiles/k_persistent_batch16_1080p_K200.md
+TRAFFIC_BYTES_PER_LAUNCH = 139.630080e6 + 40.466176e6
 
 
 def parse():
@@ -421,7 +424,7 @@ def main():
     fp32_peak = SMS * FP32_LANES * 2 * peak_clk_mhz * 1e6 / 1e12    # TFLOP/s
     achieved = smem_bytes / (k_ms / 1e3) / 1e9
     roofline = {"bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
-                "frac": achieved / smem_peak, "traffic": None,
+                "frac": achieved / smem_peak, "traffic": TRAFFIC_BYTES_PER_LAUNCH,
                 "kernel": "k_persistent", "kernel_ms": k_ms,
                 "peak_source": "derived: 152 SMs x 128 B/clk x 2070 MHz (max SM clock)",
                 "fp32": {"achieved_tflops": flops / (k_ms / 1e3) / 1e12, "peak_tflops": fp32_peak,
