@@ -253,6 +253,48 @@ def precision_sweep(fse, ctx, dev):
     return res
 
 
+def block_size_sweep(fse, ctx, dev):
+    """Mixed losses made of whole 16x16 areas (isolated and bursts, 25% of a
+    256x256 frame), concealed with blocks of 16, 8, 4 and 2 samples (d = 16,
+    K = 200): blocks/s of the persistent launch, and PSNR of the concealed
+    samples against the ground truth for line scan and optimized order
+    (Sec. 4, Table 1 compares the two orders the same way)."""
+    import torch
+    h = w = 256
+    img = fse_synth.make_image(h, w, 4242)
+    rng = np.random.default_rng(4242)
+    lost16 = fse_synth.mixed_block_mask(h // 16, w // 16, 0.25, rng)
+    mask = fse_synth.blocks_to_pixel_mask(lost16, h, w)
+    lost = mask == 1
+    gt = img[lost].astype(np.float64)
+    luma = torch.from_numpy(img).to(dev)
+    m = torch.from_numpy(mask).to(dev)
+    out = torch.empty_like(luma)
+    res = {}
+    for B in (16, 8, 4, 2):
+        row = {}
+        for oname, order in (("linescan", fse.FSE_ORDER_LINESCAN),
+                             ("optimized", fse.FSE_ORDER_OPTIMIZED)):
+            p = fse.make_params(iters=K_ITERS, order=order, block=B,
+                                executor=fse.FSE_EXEC_PERSISTENT, precision=fse.FSE_PREC_FP32,
+                                **PARAMS)
+            ms = []
+            for _ in range(2):
+                ctx.fse_conceal_batch([(luma, m, out)], p)
+                ms.append(ctx.fse_last_kernel_ms())
+            info = ctx.fse_last_batch_info()
+            torch.cuda.synchronize()
+            o = out.cpu().numpy()[lost].astype(np.float64)
+            mse = float(np.mean((o - gt) ** 2))
+            row[oname] = {"psnr_vs_truth_db": 10 * np.log10(255.0 ** 2 / mse),
+                          "blocks": info["lost_blocks"], "groups": info["groups"],
+                          "blocks_per_s": info["lost_blocks"] / (min(ms) / 1e3)}
+        row["gain_db"] = row["optimized"]["psnr_vs_truth_db"] - row["linescan"]["psnr_vs_truth_db"]
+        res[str(B)] = row
+    res["workload"] = "256x256, 25% of 16x16 areas lost (half bursts of 4-8, half isolated), K=200"
+    return res
+
+
 def serving_run(fse, rates=(50, 200, 1000), seconds=3.0, pool=12):
     """Poisson arrivals of host-memory requests (frame sizes uniform over
     352x288, 1280x720, 1920x1080, 3840x2160; 5-50% block losses, 20% with
@@ -434,8 +476,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(frames)
     sweep = None
+    bsweep = None
     if rank == 0 and not args.no_sweep:
         sweep = precision_sweep(fse, ctx, dev)
+        bsweep = block_size_sweep(fse, ctx, dev)
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
         serving = serving_run(fse)
@@ -466,6 +510,8 @@ def main():
             line["cpu_baseline"] = base
         if sweep is not None:
             line["precision_sweep"] = sweep
+        if bsweep is not None:
+            line["block_size_sweep"] = bsweep
         if serving is not None:
             line["serving"] = serving
         print(json.dumps(line), flush=True)

@@ -11,7 +11,10 @@
  *
  * Method summary (what the library computes for every lost block b):
  *   1. Extrapolation area L = block b plus a frame of `border` samples
- *      (Sec. 2, Fig. 1): 48x48 samples for 16x16 blocks and d = 16.
+ *      (Sec. 2, Fig. 1): (B + 32) x (B + 32) samples for B x B blocks and
+ *      d = 16 (48 x 48 for B = 16).  With B < d the area reaches blocks
+ *      beyond the 8-neighbourhood; blocks of one group still read the frame
+ *      as of the group start.
  *      Sub-areas: A (originally known), R (lost, concealed earlier),
  *      B_i (lost, inside b), B_o (lost, outside b, still open), and
  *      samples outside the image.
@@ -76,7 +79,7 @@ extern "C" {
 #define FSE_MAX_ITERS 1024
 
 typedef struct fse_params {
-    int block;      /* block size; 16 is the only supported value          */
+    int block;      /* block size B: 16, 8, 4 or 2 (Sec. 4 uses all four)  */
     int border;     /* frame width d around the block; 16 supported        */
     int dft;        /* DFT size per dimension; 64 supported                */
     int iters;      /* K, 0 .. FSE_MAX_ITERS (the paper uses 200)          */
@@ -148,12 +151,15 @@ int fse_conceal_batch(fse_ctx *ctx, const fse_frame *frames, int n,
 int fse_conceal_batch_host(fse_ctx *ctx, const fse_frame *frames, int n,
                            const fse_params *params, void *cuda_stream);
 
-/* FSE of n pre-gathered 48x48 areas (DEVICE pointers), for inspection and
- * parity tests of the per-block computation alone.
+/* FSE of n pre-gathered areas (DEVICE pointers), for inspection and parity
+ * tests of the per-block computation alone.  The area is M x M with
+ * M = params->block + 32, stored in the top-left of a 48x48 array.
  *   area_f   [n][48][48] float: sample values (ignored where weight is 0)
  *   area_cls [n][48][48] uint8: 0 = A, 1 = R, 2 = B_i, 3 = B_o, 4 = outside
- *   g_out    [n][16][16] float: real part of the model on the centre block,
- *                               unclamped
+ *                               (entries beyond M x M are ignored)
+ *   g_out    [n][16][16] float: real part of the model at area positions
+ *                               (16 + i, 16 + j); the block is the top-left
+ *                               B x B, unclamped
  *   u_out    [n][K] int32 (optional): selected index 64*k_m + k_n, -1 if
  *                               the area has no support
  *   dc_out   [n][K][2] float (optional): coefficient increments

@@ -53,11 +53,13 @@ static void build_twiddles(float2 *tw) {
     for (int t = 0; t < kDft; ++t) tw[t] = make_float2((float)c[t], (float)s[t]);
 }
 
-// Eq. (2) distance decay rho^dist over the 48x48 area, centre (23.5, 23.5).
-static void build_rho_table(float rho, float *tab) {
-    const double cm = 0.5 * (kArea - 1);
-    for (int m = 0; m < kArea; ++m)
-        for (int n = 0; n < kArea; ++n) {
+// Eq. (2) distance decay rho^dist over an M x M area, centre ((M-1)/2,
+// (M-1)/2), stored in the top-left of a 48x48 table.
+static void build_rho_table(float rho, int M, float *tab) {
+    const double cm = 0.5 * (M - 1);
+    for (int i = 0; i < kArea * kArea; ++i) tab[i] = 0.f;
+    for (int m = 0; m < M; ++m)
+        for (int n = 0; n < M; ++n) {
             const double dm = m - cm, dn = n - cm;
             tab[m * kArea + n] = (float)std::pow((double)rho, std::sqrt(dm * dm + dn * dn));
         }
@@ -121,17 +123,19 @@ void fse_ctx::host_release(HostBuf &b) {
     b.cap = 0;
 }
 
-const float *fse_ctx::rho_table(float rho, int *rc) {
+const float *fse_ctx::rho_table(float rho, int block, int *rc) {
+    // cache key: rho and the area size (block + 32)
+    const float key = rho + 16.f * (float)block;
     {
         std::lock_guard<std::mutex> lk(mem_mu);
         for (auto &e : rho_tabs)
-            if (e.first == rho) return static_cast<const float *>(e.second.ptr);
+            if (e.first == key) return static_cast<const float *>(e.second.ptr);
     }
     DevBuf b;
     *rc = dev_reserve(b, kArea * kArea * sizeof(float));
     if (*rc) return nullptr;
     std::vector<float> tab(kArea * kArea);
-    build_rho_table(rho, tab.data());
+    build_rho_table(rho, block + 2 * kBorder, tab.data());
     if (cudaMemcpy(b.ptr, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) !=
         cudaSuccess) {
         cudaGetLastError();
@@ -140,7 +144,7 @@ const float *fse_ctx::rho_table(float rho, int *rc) {
         return nullptr;
     }
     std::lock_guard<std::mutex> lk(mem_mu);
-    rho_tabs.emplace_back(rho, b);
+    rho_tabs.emplace_back(key, b);
     return static_cast<const float *>(b.ptr);
 }
 
@@ -183,7 +187,7 @@ const uint4 *fse_ctx::frag_table(int precision, int *rc) {
 
 int fse::check_params(const fse_params *p) {
     if (!p) return FSE_EINVAL;
-    if (p->block != kBlock || p->border != kBorder || p->dft != kDft) return FSE_EINVAL;
+    if (block_log2(p->block) < 0 || p->border != kBorder || p->dft != kDft) return FSE_EINVAL;
     if (p->iters < 0 || p->iters > FSE_MAX_ITERS) return FSE_EINVAL;
     if (!(p->rho > 0.f && p->rho < 1.f)) return FSE_EINVAL;
     if (!(p->delta >= 0.f && p->delta <= 1.f)) return FSE_EINVAL;
@@ -217,7 +221,7 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
                    const fse_params *p, cudaStream_t stream,
                    const std::vector<std::vector<uint8_t>> *host_lost) {
     int rc = FSE_OK;
-    const float *rho_tab = ctx->rho_table(p->rho, &rc);
+    const float *rho_tab = ctx->rho_table(p->rho, p->block, &rc);
     if (!rho_tab) return rc;
     const uint4 *frags = ctx->frag_table(p->precision, &rc);
     if (rc) return rc;
@@ -241,8 +245,10 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
         d.W = frames[i].width;
         d.stride = frames[i].stride;
         d.wstride = (d.W + 31) & ~31;
-        d.bh = (d.H + kBlock - 1) / kBlock;
-        d.bw = (d.W + kBlock - 1) / kBlock;
+        d.lb = block_log2(p->block);
+        d.pad0 = 0;
+        d.bh = (d.H + p->block - 1) / p->block;
+        d.bw = (d.W + p->block - 1) / p->block;
         lost_off[i + 1] = lost_off[i] + d.bh * d.bw;
         work_floats += (size_t)d.H * d.wstride;
         max_rows_x_bw = std::max(max_rows_x_bw, d.H * d.bw);
@@ -379,8 +385,10 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
             const int f = items[k].x, b = items[k].y;
             const int bw = fd[f].bw, bh = fd[f].bh, by = b / bw, bx = b % bw;
             const int g = gob_h[lost_off[f] + b];
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
+            // blocks whose samples lie in this block's area: +-16/B blocks
+            const int rad = kBorder / p->block;
+            for (int dy = -rad; dy <= rad; ++dy)
+                for (int dx = -rad; dx <= rad; ++dx) {
                     if (!(dy | dx)) continue;
                     const int ny = by + dy, nx = bx + dx;
                     if (ny < 0 || ny >= bh || nx < 0 || nx >= bw) continue;
@@ -444,7 +452,7 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
     }
 
     // ---- extrapolation ----
-    const KParams kp{p->rho, p->delta, p->gamma, p->iters, frags};
+    const KParams kp{p->rho, p->delta, p->gamma, p->iters, frags, block_log2(p->block)};
     const FrameDesc *fdev = static_cast<const FrameDesc *>(ws.frames.ptr);
     const float2 *tw_tab = static_cast<const float2 *>(ctx->tw_dev.ptr);
     int launches = 1;  // block-loss map
@@ -670,11 +678,12 @@ extern "C" int fse_extrapolate_areas(fse_ctx *ctx, const float *area_f,
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(ctx->api_mu);
     cudaSetDevice(ctx->device);
-    const float *rho_tab = ctx->rho_table(params->rho, &rc);
+    const float *rho_tab = ctx->rho_table(params->rho, params->block, &rc);
     if (!rho_tab) return rc;
     const uint4 *frags = ctx->frag_table(params->precision, &rc);
     if (rc) return rc;
-    const KParams kp{params->rho, params->delta, params->gamma, params->iters, frags};
+    const KParams kp{params->rho, params->delta, params->gamma, params->iters, frags,
+                     block_log2(params->block)};
     CK(launch_areas(area_f, area_cls, n, kp, rho_tab,
                     static_cast<const float2 *>(ctx->tw_dev.ptr), params->precision, g_out,
                     u_out, dc_out, r_out, static_cast<cudaStream_t>(cuda_stream)));

@@ -77,7 +77,7 @@ struct fse_ctx {
     bool keep_trace = false;
 
     fse::DevBuf tw_dev;                                   // 64 twiddles
-    std::vector<std::pair<float, fse::DevBuf>> rho_tabs;  // Eq. (2) decay per rho
+    std::vector<std::pair<float, fse::DevBuf>> rho_tabs;  // Eq. (2) decay per (rho, block)
     fse::DevBuf frags[5];                                 // per precision (tensor cores)
     fse::Workspace ws;  // synchronous API
     std::mutex api_mu;  // one synchronous API call at a time
@@ -105,7 +105,7 @@ struct fse_ctx {
     void host_release(fse::HostBuf &b);
     // Device table of rho^dist for this rho (created once, kept until
     // destroy); nullptr on failure.
-    const float *rho_table(float rho, int *rc);
+    const float *rho_table(float rho, int block, int *rc);
     // Packed DFT operand fragments of the tensor-core projection for this
     // precision (built once); nullptr for FSE_PREC_FP32 or on failure.
     const uint4 *frag_table(int precision, int *rc);

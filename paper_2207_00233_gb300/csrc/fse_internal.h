@@ -56,7 +56,15 @@ struct KParams {
     int iters;
     const uint4 *frags;  // packed DFT operand fragments of the tensor-core
                          // projection (null for FSE_PREC_FP32)
+    int lb;              // log2 of the block size B; the area is (B + 32)^2
 };
+
+// Block sizes: B = 16 (the 48x48 area fills the tile) or B = 8, 4, 2 with the
+// same 16-sample frame: the (B + 32)^2 area occupies the top-left of the
+// 48x48 tile and the rest weighs 0 (the zero-extended DFT is unchanged).
+inline int block_log2(int block) {
+    return block == 16 ? 4 : block == 8 ? 3 : block == 4 ? 2 : block == 2 ? 1 : -1;
+}
 
 // Tensor-core projection (warp-level mma.sync).  Stage 1 multiplies the
 // stacked area tiles [w*f; w] (96 x 48) by [cos | -sin] (48 x 80, half
@@ -82,6 +90,8 @@ struct FrameDesc {
     const int32_t *gob;      // [bh][bw] group of each block, -1 = no loss
     int H, W, stride, wstride, bh, bw;
     int16_t *trace;          // [bh*bw][iters] selected indices, or null
+    int lb;                  // log2 of the block size B (1..4)
+    int pad0;
 };
 
 // Dependency graph of the persistent executor: items are (frame, block)

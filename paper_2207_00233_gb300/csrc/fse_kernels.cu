@@ -78,18 +78,19 @@ struct FrameSrc {
         : fd(f), by(block / f.bw), bx(block % f.bw), self(block), gself(f.gob[block]) {}
 
     __device__ void gather(float *xt, float *wt, const float *rho_tab, float delta) const {
-        const int y0 = by * kBlock - kBorder, x0 = bx * kBlock - kBorder;
+        const int B = 1 << fd.lb, M = B + 2 * kBorder;
+        const int y0 = by * B - kBorder, x0 = bx * B - kBorder;
         for (int p = threadIdx.x; p < kArea * kArea; p += kThreads) {
             const int m = p / kArea, n = p - m * kArea;
             const int y = y0 + m, x = x0 + n;
             float w = 0.f, v = 0.f;
-            if (y >= 0 && y < fd.H && x >= 0 && x < fd.W) {
+            if (m < M && n < M && y >= 0 && y < fd.H && x >= 0 && x < fd.W) {
                 const size_t q = (size_t)y * fd.stride + x;
                 if (!fd.mask[q]) {
                     w = rho_tab[p];
                     v = (float)fd.luma[q];
                 } else {
-                    const int cb = (y / kBlock) * fd.bw + (x / kBlock);
+                    const int cb = (y >> fd.lb) * fd.bw + (x >> fd.lb);
                     if (cb != self) {
                         const int gc = fd.gob[cb];
                         if (gc >= 0 && gc < gself) {
@@ -107,7 +108,8 @@ struct FrameSrc {
     // Thread t holds the model value of sample (t / 16, t % 16) of the block.
     __device__ void store(float g) const {
         const int i = threadIdx.x >> 4, j = threadIdx.x & 15;
-        const int y = by * kBlock + i, x = bx * kBlock + j;
+        if (i >= (1 << fd.lb) || j >= (1 << fd.lb)) return;
+        const int y = (by << fd.lb) + i, x = (bx << fd.lb) + j;
         if (y >= fd.H || x >= fd.W) return;
         const size_t q = (size_t)y * fd.stride + x;
         if (!fd.mask[q]) return;
@@ -122,11 +124,13 @@ struct AreaSrc {
     const float *f;
     const uint8_t *cls;
     float *g;
+    int lb;
 
     __device__ void gather(float *xt, float *wt, const float *rho_tab, float delta) const {
+        const int M = (1 << lb) + 2 * kBorder;
         for (int p = threadIdx.x; p < kArea * kArea; p += kThreads) {
             const int m = p / kArea, n = p - m * kArea;
-            const int c = cls[p];
+            const int c = (m < M && n < M) ? cls[p] : 4;
             float w = 0.f;
             if (c == 0) w = rho_tab[p];
             else if (c == 1) w = delta * rho_tab[p];
@@ -647,21 +651,19 @@ __device__ __forceinline__ float run_block(const Src &src, const KParams &kp,
                     }
                 }
             }
+            // the lane holding the warp's smallest index writes its candidate
             const uint32_t wk = __reduce_min_sync(0xffffffffu, kk);
-            const int src_lane = __ffs(__ballot_sync(0xffffffffu, kk == wk)) - 1;
-            cre = __shfl_sync(0xffffffffu, cre, src_lane);
-            cim = __shfl_sync(0xffffffffu, cim, src_lane);
-            if (l == 0) cand[w] = make_float4(__uint_as_float(wk), cre, cim, 0.f);
+            if (kk == wk) cand[w] = make_float4(__uint_as_float(wk), cre, cim, 0.f);
         } else if (l == 0) {
             cand[w].x = __uint_as_float(0xffffffffu);
         }
         __syncthreads();
-        // lanes 0..7 read the eight warp candidates; the smallest index wins
-        const float4 c = l < kWarps ? cand[l] : make_float4(__uint_as_float(0xffffffffu), 0.f, 0.f, 0.f);
-        const uint32_t u = __reduce_min_sync(0xffffffffu, __float_as_uint(c.x));
-        const int win = __ffs(__ballot_sync(0xffffffffu, __float_as_uint(c.x) == u)) - 1;
-        const float dcr = __shfl_sync(0xffffffffu, c.y, win) * gw;
-        const float dci = __shfl_sync(0xffffffffu, c.z, win) * gw;
+        // lanes 0..7 read the eight warp candidates; the smallest index wins.
+        // Warp w owns indices [512 w, 512 w + 512), so the winner's slot is u >> 9.
+        const uint32_t u = __reduce_min_sync(
+            0xffffffffu, l < kWarps ? __float_as_uint(cand[l].x) : 0xffffffffu);
+        const float4 cw = cand[(u >> 9) & (kWarps - 1)];
+        const float dcr = cw.y * gw, dci = cw.z * gw;
         if (tid == 0) {
             dcl[it] = make_float2(dcr, dci);
             ul[it] = (uint16_t)u;
@@ -821,7 +823,7 @@ k_areas(const float *area_f, const uint8_t *area_cls, KParams kp, const float *r
     extern __shared__ __align__(16) unsigned char smem[];
     const size_t a = blockIdx.x;
     const AreaSrc src{area_f + a * kArea * kArea, area_cls + a * kArea * kArea,
-                      g_out + a * kBlock * kBlock};
+                      g_out + a * kBlock * kBlock, kp.lb};
     const Trace tr{u_out ? u_out + a * kp.iters : nullptr,
                    dc_out ? dc_out + a * kp.iters * 2 : nullptr,
                    r_out ? r_out + a * kDft * kDft * 2 : nullptr};
@@ -836,11 +838,12 @@ __global__ void k_block_loss(const FrameDesc *frames, uint8_t *lost, const int *
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= fd.H * fd.bw) return;
     const int y = idx / fd.bw, bx = idx - y * fd.bw;
-    const uint8_t *row = fd.mask + (size_t)y * fd.stride + bx * kBlock;
-    const int n = min(kBlock, fd.W - bx * kBlock);
+    const int B = 1 << fd.lb;
+    const uint8_t *row = fd.mask + (size_t)y * fd.stride + bx * B;
+    const int n = min(B, fd.W - bx * B);
     int any = 0;
     for (int i = 0; i < n; ++i) any |= row[i];
-    if (any) lost[lost_off[blockIdx.y] + (y / kBlock) * fd.bw + bx] = 1;
+    if (any) lost[lost_off[blockIdx.y] + (y >> fd.lb) * fd.bw + bx] = 1;
 }
 
 }  // namespace

@@ -193,7 +193,7 @@ extern "C" int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_param
     if (!frame) return FSE_EINVAL;
     int rc = check_params(params);
     if (rc) return rc;
-    if (params->precision != FSE_PREC_FP32) return FSE_EINVAL;
+    if (params->precision != FSE_PREC_FP32 || params->block != kBlock) return FSE_EINVAL;
     if (!frame->luma || !frame->out || !frame->loss_mask || frame->width <= 0 ||
         frame->height <= 0 || frame->stride < frame->width)
         return FSE_EINVAL;
@@ -234,6 +234,8 @@ extern "C" int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_param
     h_desc.bh = bh;
     h_desc.bw = bw;
     h_desc.trace = nullptr;
+    h_desc.lb = block_log2(kBlock);
+    h_desc.pad0 = 0;
     na_twiddles(h_tw);
     const double cm = 0.5 * (kArea - 1);
     for (int m = 0; m < kArea; ++m)
@@ -268,7 +270,8 @@ extern "C" int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_param
     if (frame->out != frame->luma)
         NA_CK(cudaMemcpy2DAsync(frame->out, frame->stride, frame->luma, frame->stride, W, H,
                                 cudaMemcpyDeviceToDevice, stream));
-    const KParams kp{params->rho, params->delta, params->gamma, params->iters, nullptr};
+    const KParams kp{params->rho, params->delta, params->gamma, params->iters, nullptr,
+                     block_log2(kBlock)};
     for (int g = 0; g < n_groups; ++g)
         NA_CK(launch_group(d_desc, d_items + h_group_start[g],
                            h_group_start[g + 1] - h_group_start[g], kp, d_rho, d_tw,

@@ -37,14 +37,14 @@ size_t frame_bytes(const fse_frame &f) {
 }
 
 // Block-loss map of a host frame.
-std::vector<uint8_t> host_block_loss(const fse_frame &f) {
-    const int bh = (f.height + kBlock - 1) / kBlock, bw = (f.width + kBlock - 1) / kBlock;
+std::vector<uint8_t> host_block_loss(const fse_frame &f, int B) {
+    const int bh = (f.height + B - 1) / B, bw = (f.width + B - 1) / B;
     std::vector<uint8_t> lost((size_t)bh * bw, 0);
     for (int y = 0; y < f.height; ++y) {
         const uint8_t *row = f.loss_mask + (size_t)y * f.stride;
-        uint8_t *lrow = lost.data() + (size_t)(y / kBlock) * bw;
+        uint8_t *lrow = lost.data() + (size_t)(y / B) * bw;
         for (int bx = 0; bx < bw; ++bx) {
-            const int x0 = bx * kBlock, x1 = std::min(f.width, x0 + kBlock);
+            const int x0 = bx * B, x1 = std::min(f.width, x0 + B);
             uint8_t any = 0;
             for (int x = x0; x < x1; ++x) any |= row[x];
             if (any) lrow[bx] = 1;
@@ -101,7 +101,7 @@ int launch_batch(fse_ctx *ctx, Slot &s) {
             std::memcpy(pl + (size_t)y * h.width, h.luma + (size_t)y * h.stride, h.width);
             std::memcpy(pm + (size_t)y * h.width, h.loss_mask + (size_t)y * h.stride, h.width);
         }
-        lost[i] = host_block_loss(h);
+        lost[i] = host_block_loss(h, r->params.block);
         uint8_t *dl = static_cast<uint8_t *>(ws.d_luma.ptr) + r->io_off;
         uint8_t *dm = static_cast<uint8_t *>(ws.d_mask.ptr) + r->io_off;
         uint8_t *dout = static_cast<uint8_t *>(ws.d_out.ptr) + r->io_off;
@@ -112,12 +112,9 @@ int launch_batch(fse_ctx *ctx, Slot &s) {
             return FSE_ECUDA;
         }
         dev[i] = fse_frame{dl, dout, dm, h.width, h.height, h.width};
-        const int bh = (h.height + kBlock - 1) / kBlock, bw = (h.width + kBlock - 1) / kBlock;
         int cnt = 0;
         for (uint8_t v : lost[i]) cnt += v != 0;
         r->stats.lost_blocks = cnt;
-        (void)bh;
-        (void)bw;
     }
     const fse_params p = s.reqs[0]->params;
     rc = run_batch(ctx, ws, dev.data(), n, &p, s.stream, &lost);

@@ -50,7 +50,8 @@ def gpu_conceal(ctx, frames, params, want_work=True, want_trace=False):
             works.append(w)
         if want_trace:
             h, wd = l.shape
-            nb = ((h + 15) // 16) * ((wd + 15) // 16)
+            B = params.block
+            nb = ((h + B - 1) // B) * ((wd + B - 1) // B)
             t = torch.empty(nb * max(params.iters, 1), dtype=torch.int16, device=dev)
             ctx.fse_copy_trace(i, t)
             torch.cuda.synchronize()
@@ -92,7 +93,8 @@ def compare_frame(img, mask, params, out, work, g_trace, o_work, o_trace, gob, l
     with the oracle; validity on the others.  Returns a statistics dict."""
     check_output_basics(img, mask, out, work, label)
     bh, bw = gob.shape
-    K = params.iters
+    B, d = params.block, params.border
+    rad = d // B                     # blocks whose samples are in the area
     lost_blocks = [(int(gob[by, bx]), by, bx) for by in range(bh) for bx in range(bw)
                    if gob[by, bx] >= 0]
     lost_blocks.sort()
@@ -104,14 +106,14 @@ def compare_frame(img, mask, params, out, work, g_trace, o_work, o_trace, gob, l
         b = by * bw + bx
         same = np.array_equal(g_trace[b], o_trace[b])
         up_clean = True
-        for dy in (-1, 0, 1):
-            for dx in (-1, 0, 1):
+        for dy in range(-rad, rad + 1):
+            for dx in range(-rad, rad + 1):
                 ny, nx = by + dy, bx + dx
                 if (dy or dx) and 0 <= ny < bh and 0 <= nx < bw:
                     if 0 <= gob[ny, nx] < g and not clean[ny, nx]:
                         up_clean = False
-        ys = slice(by * 16, min(by * 16 + 16, img.shape[0]))
-        xs = slice(bx * 16, min(bx * 16 + 16, img.shape[1]))
+        ys = slice(by * B, min(by * B + B, img.shape[0]))
+        xs = slice(bx * B, min(bx * B + B, img.shape[1]))
         lm = mask[ys, xs] != 0
         if same and up_clean:
             clean[by, bx] = True
@@ -121,8 +123,9 @@ def compare_frame(img, mask, params, out, work, g_trace, o_work, o_trace, gob, l
             stats["max_err_clean"] = max(stats["max_err_clean"], float(e.max()))
             continue
         # not unique: the GPU result must be a valid trajectory on its inputs
-        f, cls = area_from_frame(img, mask, work, gob, by, bx)
-        worst, gv = trajectory(f, cls, g_trace[b], params.rho, params.delta, params.gamma)
+        f, cls = area_from_frame(img, mask, work, gob, by, bx, B, d)
+        worst, gv = trajectory(f, cls, g_trace[b], params.rho, params.delta, params.gamma,
+                               B=B, d=d)
         assert worst <= 1.0, f"{label}: block ({by},{bx}) selection off by {worst:.2f} tau"
         gi = np.clip(gv, 0, 255)[:lm.shape[0], :lm.shape[1]]
         ev = float(np.abs(gi[lm] - work[ys, xs][lm]).max())
@@ -131,7 +134,7 @@ def compare_frame(img, mask, params, out, work, g_trace, o_work, o_trace, gob, l
         stats["max_err_valid"] = max(stats["max_err_valid"], ev)
         if up_clean:
             stats["roots"] += 1
-            fo, clso = area_from_frame(img, mask, o_work, gob, by, bx)
+            fo, clso = area_from_frame(img, mask, o_work, gob, by, bx, B, d)
             it, tie = near_tie_at_divergence(fo, clso, g_trace[b], o_trace[b], params.rho,
                                              params.delta, params.gamma)
             assert tie <= 1.0, f"{label}: block ({by},{bx}) diverged at it {it} by {tie:.2f} tau"

@@ -259,7 +259,7 @@ def test_invalid_params_rejected(fse, ctx):
     out = np.empty_like(img)
     bad = [dict(iters=-1), dict(iters=fse.FSE_MAX_ITERS + 1), dict(rho=1.0), dict(rho=0.0),
            dict(delta=1.5), dict(gamma=0.0), dict(order=3), dict(executor=9),
-           dict(block=8), dict(border=8), dict(dft=32), dict(precision=42)]
+           dict(block=3), dict(block=32), dict(border=8), dict(dft=32), dict(precision=42)]
     for kw in bad:
         p = fse.make_params(**{**dict(iters=10), **kw})
         with pytest.raises(fse.FseError) as e:
