@@ -202,6 +202,7 @@ static int check_frame(const fse_frame &f) {
     if (!f.luma || !f.out || !f.loss_mask) return FSE_EINVAL;
     if (f.width <= 0 || f.height <= 0 || f.stride < f.width) return FSE_EINVAL;
     if ((long long)f.width * f.height > (1LL << 30)) return FSE_EINVAL;
+    if ((long long)f.height * f.stride >= (1LL << 31)) return FSE_EINVAL;  // 32-bit offsets
     return FSE_OK;
 }
 

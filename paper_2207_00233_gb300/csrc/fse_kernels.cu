@@ -756,12 +756,18 @@ __global__ void __launch_bounds__(kThreads, 3)
 k_group(const FrameDesc *frames, const int2 *items, KParams kp, const float *rho_tab,
         const float2 *tw_tab) {
     extern __shared__ __align__(16) unsigned char smem[];
+    float g;
+    {
+        const int2 item = items[blockIdx.x];
+        const FrameSrc src(frames[item.x], item.y);
+        g = run_block<P, false>(src, kp, rho_tab, tw_tab, smem, Trace{nullptr, nullptr, nullptr});
+    }
+    // Reload the item instead of keeping it live through the iterations.
+    asm volatile("" ::: "memory");
     const int2 item = items[blockIdx.x];
-    const FrameDesc &fd = frames[item.x];
-    const FrameSrc src(fd, item.y);
-    const float g = run_block<P, false>(src, kp, rho_tab, tw_tab, smem, Trace{nullptr, nullptr, nullptr});
+    const FrameSrc src(frames[item.x], item.y);
     src.store(g);
-    write_frame_trace(fd, item.y, kp, smem);
+    write_frame_trace(frames[item.x], item.y, kp, smem);
 }
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
@@ -801,12 +807,18 @@ k_persistent(const FrameDesc *frames, DepGraph dg, KParams kp, const float *rho_
         __syncthreads();
         const int i = s_item;
         if (i >= dg.n || !s_ok) break;
-        const int2 item = dg.items[i];
-        const FrameDesc &fd = frames[item.x];
-        const FrameSrc src(fd, item.y);
-        const float g = run_block<P, false>(src, kp, rho_tab, tw_tab, smem, Trace{nullptr, nullptr, nullptr});
+        float g;
+        {
+            const int2 item = dg.items[i];
+            const FrameSrc src(frames[item.x], item.y);
+            g = run_block<P, false>(src, kp, rho_tab, tw_tab, smem, Trace{nullptr, nullptr, nullptr});
+        }
+        // Reload the item instead of keeping it live through the iterations.
+        asm volatile("" ::: "memory");
+        const int2 item = dg.items[s_item];
+        const FrameSrc src(frames[item.x], item.y);
         src.store(g);
-        write_frame_trace(fd, item.y, kp, smem);
+        write_frame_trace(frames[item.x], item.y, kp, smem);
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {

@@ -281,7 +281,8 @@ extern "C" int fse_submit(fse_ctx *ctx, const fse_frame *frame, const fse_params
     int rc = check_params(params);
     if (rc) return rc;
     if (!frame->luma || !frame->out || !frame->loss_mask || frame->width <= 0 ||
-        frame->height <= 0 || frame->stride < frame->width)
+        frame->height <= 0 || frame->stride < frame->width ||
+        (long long)frame->height * frame->stride >= (1LL << 31))
         return FSE_EINVAL;
     std::lock_guard<std::mutex> lk(ctx->mu);
     if (ctx->stop) return FSE_EINVAL;
