@@ -43,8 +43,9 @@ SMS = 152
 SMEM_BYTES_PER_CLK = 128
 FP32_LANES = 128
 # DRAM bytes (read + write) of one k_persistent<FP32> launch on this workload,
-# from the ncu capture summarised in profiles/k_persistent_batch16_1080p_K200.md
-TRAFFIC_BYTES_PER_LAUNCH = 139.630080e6 + 40.466176e6
+# from the ncu capture summarised in profiles/k_persistent_batch16_1080p_K200.md;
+# None while the kernel differs from the captured one
+TRAFFIC_BYTES_PER_LAUNCH = None
 
 
 def parse():

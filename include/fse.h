@@ -73,8 +73,9 @@ extern "C" {
 /* How the groups are dispatched on the device. */
 #define FSE_EXEC_GROUPS 0      /* one launch per group (plain path)              */
 #define FSE_EXEC_PERSISTENT 1  /* one persistent launch over all frames; a block
-                                  starts once its earlier-group neighbours are
-                                  done (device dependency counters)            */
+                                  starts once every earlier-group block whose
+                                  samples lie in its area has published its
+                                  completion flag (bounded device waits)      */
 
 #define FSE_MAX_ITERS 1024
 

@@ -369,55 +369,24 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
     }
     group_start[max_groups] = (int)items.size();
 
-    // Dependency graph for the persistent executor: for every item, the lost
-    // 8-neighbours of earlier groups (predecessors) and of later groups
-    // (successors).  Items are in group order, so every predecessor of an
-    // item precedes it in the claim order.
-    std::vector<int> deps, succ_ptr, succ;
     const bool persistent = p->executor == FSE_EXEC_PERSISTENT;
-    if (persistent && lost_blocks > 0) {
-        std::vector<int> item_of(nblocks, -1);
-        for (int k = 0; k < (int)items.size(); ++k)
-            item_of[lost_off[items[k].x] + items[k].y] = k;
-        deps.assign(items.size(), 0);
-        succ_ptr.assign(items.size() + 1, 0);
-        succ.reserve(items.size() * 4);
-        for (int k = 0; k < (int)items.size(); ++k) {
-            const int f = items[k].x, b = items[k].y;
-            const int bw = fd[f].bw, bh = fd[f].bh, by = b / bw, bx = b % bw;
-            const int g = gob_h[lost_off[f] + b];
-            // blocks whose samples lie in this block's area: +-16/B blocks
-            const int rad = kBorder / p->block;
-            for (int dy = -rad; dy <= rad; ++dy)
-                for (int dx = -rad; dx <= rad; ++dx) {
-                    if (!(dy | dx)) continue;
-                    const int ny = by + dy, nx = bx + dx;
-                    if (ny < 0 || ny >= bh || nx < 0 || nx >= bw) continue;
-                    const int gn = gob_h[lost_off[f] + ny * bw + nx];
-                    if (gn < 0) continue;
-                    if (gn < g) deps[k] += 1;
-                    else if (gn > g) succ.push_back(item_of[lost_off[f] + ny * bw + nx]);
-                }
-            succ_ptr[k + 1] = (int)succ.size();
-        }
-    }
 
     // ---- uploads ----
     const size_t n_items = items.size();
     rc = ctx->dev_reserve(ws.items, sizeof(int2) * std::max<size_t>(n_items, 1));
-    if (!rc && persistent) {
-        rc = ctx->dev_reserve(ws.deps, sizeof(int) * std::max<size_t>(n_items, 1));
-        if (!rc) rc = ctx->dev_reserve(ws.succ_ptr, sizeof(int) * (n_items + 1));
-        if (!rc) rc = ctx->dev_reserve(ws.succ, sizeof(int) * std::max<size_t>(succ.size(), 1));
-    }
+    if (!rc && persistent) rc = ctx->dev_reserve(ws.done, sizeof(uint32_t) * nblocks);
     if (rc) return rc;
+    int stuck_item = -1;
     if (persistent && ctx->test_stuck_dep && n_items > 0) {
-        deps[n_items - 1] += 1;  // nothing ever releases this dependency
+        stuck_item = (int)n_items - 1;  // waits on a flag nothing sets
         ctx->test_stuck_dep = false;
     }
+    {
+        uint32_t *dp = static_cast<uint32_t *>(ws.done.ptr);
+        for (int i = 0; i < n; ++i) fd[i].done = persistent ? dp + lost_off[i] : nullptr;
+    }
     const size_t stage_bytes = sizeof(FrameDesc) * n + sizeof(int32_t) * nblocks +
-                               sizeof(int2) * n_items + sizeof(int) * (2 * n_items + 1) +
-                               sizeof(int) * succ.size() + 256;
+                               sizeof(int2) * n_items + 256;
     rc = ctx->host_reserve(ws.stage, stage_bytes);
     if (rc) return rc;
     char *st = static_cast<char *>(ws.stage.ptr);
@@ -435,12 +404,9 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
     rc = put(ws.frames.ptr, fd.data(), sizeof(FrameDesc) * n);
     if (!rc) rc = put(ws.gob.ptr, gob_h.data(), sizeof(int32_t) * nblocks);
     if (!rc) rc = put(ws.items.ptr, items.data(), sizeof(int2) * n_items);
-    if (!rc && persistent && n_items > 0) {
-        rc = put(ws.deps.ptr, deps.data(), sizeof(int) * n_items);
-        if (!rc) rc = put(ws.succ_ptr.ptr, succ_ptr.data(), sizeof(int) * (n_items + 1));
-        if (!rc) rc = put(ws.succ.ptr, succ.data(), sizeof(int) * succ.size());
-    }
     if (rc) return rc;
+    if (persistent && nblocks > 0)
+        CK(cudaMemsetAsync(ws.done.ptr, 0, sizeof(uint32_t) * nblocks, stream));
     if (!ws.staged) CK(cudaEventCreateWithFlags(&ws.staged, cudaEventDisableTiming));
     CK(cudaEventRecord(ws.staged, stream));
 
@@ -467,19 +433,17 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
         if (persistent) {
             int *status = static_cast<int *>(ws.status.ptr);
             CK(cudaMemsetAsync(status, 0, sizeof(int) * 2, stream));
-            DepGraph dg;
-            dg.items = static_cast<const int2 *>(ws.items.ptr);
-            dg.deps = static_cast<int *>(ws.deps.ptr);
-            dg.succ_ptr = static_cast<const int *>(ws.succ_ptr.ptr);
-            dg.succ = static_cast<const int *>(ws.succ.ptr);
-            dg.head = status;
-            dg.error = status + 1;
-            dg.n = (int)n_items;
-            dg.spin_limit = ctx->spin_limit;
+            WorkQueue wq;
+            wq.items = static_cast<const int2 *>(ws.items.ptr);
+            wq.head = status;
+            wq.error = status + 1;
+            wq.n = (int)n_items;
+            wq.stuck_item = stuck_item;
+            wq.spin_limit = ctx->spin_limit;
             int per_sm = max_resident_ctas(p->iters);
             if (ctx->persistent_ctas > 0) per_sm = std::min(per_sm, ctx->persistent_ctas);
             const int grid = std::min<int>((int)n_items, ctx->num_sms * per_sm);
-            CK(launch_persistent(fdev, dg, kp, rho_tab, tw_tab, p->precision, grid, stream));
+            CK(launch_persistent(fdev, wq, kp, rho_tab, tw_tab, p->precision, grid, stream));
             ws.status_live = true;
             launches += 1;
         } else {
@@ -537,9 +501,7 @@ void fse::release_workspace(fse_ctx *ctx, Workspace &ws) {
     ctx->dev_release(ws.lost_off);
     ctx->dev_release(ws.gob);
     ctx->dev_release(ws.items);
-    ctx->dev_release(ws.deps);
-    ctx->dev_release(ws.succ_ptr);
-    ctx->dev_release(ws.succ);
+    ctx->dev_release(ws.done);
     ctx->dev_release(ws.status);
     ctx->dev_release(ws.trace);
     ctx->dev_release(ws.d_luma);

@@ -27,7 +27,7 @@ struct HostBuf {
 
 // Everything one in-flight batch needs on the device.
 struct Workspace {
-    DevBuf frames, work, lost, lost_off, gob, items, deps, succ_ptr, succ, status, trace;
+    DevBuf frames, work, lost, lost_off, gob, items, done, status, trace;
     DevBuf d_luma, d_mask, d_out;  // device copies of host frames
     HostBuf stage;                 // pinned staging for uploads / readback
     HostBuf io;                    // pinned staging of serving frames

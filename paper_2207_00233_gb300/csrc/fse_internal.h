@@ -90,22 +90,22 @@ struct FrameDesc {
     const int32_t *gob;      // [bh][bw] group of each block, -1 = no loss
     int H, W, stride, wstride, bh, bw;
     int16_t *trace;          // [bh*bw][iters] selected indices, or null
+    uint32_t *done;          // [bh*bw] completion flags (persistent executor)
     int lb;                  // log2 of the block size B (1..4)
     int pad0;
 };
 
-// Dependency graph of the persistent executor: items are (frame, block)
-// pairs sorted by group; deps[i] counts the lost 8-neighbours of item i
-// from earlier groups still to finish; succ lists the later-group lost
-// 8-neighbours of every item (CSR).
-struct DepGraph {
+// Work of the persistent executor: items are (frame, block) pairs in group
+// order.  A claimed item waits until every earlier-group lost block whose
+// samples lie in its area has set its completion flag; claims follow the
+// group order, so every awaited block was claimed earlier by a running CTA.
+struct WorkQueue {
     const int2 *items;       // [n] (frame, block)
-    int *deps;               // [n]
-    const int *succ_ptr;     // [n+1]
-    const int *succ;         // [succ_ptr[n]]
     int *head;               // work counter
     int *error;              // status word: 0 ok, else FSE_ETIMEDOUT
     int n;
+    int stuck_item;          // test hook: this item also waits on its own
+                             // flag, which nothing sets (-1: none)
     long long spin_limit;    // polls before a wait gives up
 };
 
@@ -119,7 +119,7 @@ cudaError_t launch_group(const FrameDesc *frames_dev, const int2 *items,
                          int n_items, const KParams &kp, const float *rho_tab,
                          const float2 *tw_tab, int precision,
                          cudaStream_t stream);
-cudaError_t launch_persistent(const FrameDesc *frames_dev, const DepGraph &dg,
+cudaError_t launch_persistent(const FrameDesc *frames_dev, const WorkQueue &wq,
                               const KParams &kp, const float *rho_tab,
                               const float2 *tw_tab, int precision, int grid,
                               cudaStream_t stream);

@@ -770,61 +770,88 @@ k_group(const FrameDesc *frames, const int2 *items, KParams kp, const float *rho
     write_frame_trace(frames[item.x], item.y, kp, smem);
 }
 
-__device__ __forceinline__ int ld_acquire(const int *p) {
-    int v;
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
     asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+// Warp 0 waits, with bounded polling, for the completion flags of the
+// earlier-group lost blocks whose samples lie in the area of `block`
+// (+-16/B blocks).  Returns false when a wait gave up or another CTA
+// reported an error.
+__device__ __forceinline__ bool wait_area(const FrameDesc &fd, int block, bool stuck,
+                                          const WorkQueue &q) {
+    const int lane = threadIdx.x & 31;
+    const int rad = kBorder >> fd.lb, side = 2 * rad + 1;
+    const int by = block / fd.bw, bx = block - by * fd.bw;
+    const int gself = fd.gob[block];
+    bool ok = true;
+    for (int p = lane; p < side * side + (stuck ? 1 : 0) && ok; p += 32) {
+        int c;
+        if (p == side * side) {
+            c = block;  // test hook: a flag nothing sets before this wait ends
+        } else {
+            const int ny = by + p / side - rad, nx = bx + p % side - rad;
+            if (ny < 0 || ny >= fd.bh || nx < 0 || nx >= fd.bw || (ny == by && nx == bx))
+                continue;
+            c = ny * fd.bw + nx;
+            const int gc = fd.gob[c];
+            if (gc < 0 || gc >= gself) continue;
+        }
+        long long spins = 0;
+        while (ld_acquire_u32(fd.done + c) == 0u) {
+            if (++spins > q.spin_limit) {
+                atomicExch(q.error, FSE_ETIMEDOUT);
+                ok = false;
+                break;
+            }
+            if ((spins & 255) == 0 && *(volatile int *)q.error) {
+                ok = false;
+                break;
+            }
+            __nanosleep(200);
+        }
+    }
+    return __all_sync(0xffffffffu, ok);
 }
 
 template <int P>
 __global__ void __launch_bounds__(kThreads, 3)
-k_persistent(const FrameDesc *frames, DepGraph dg, KParams kp, const float *rho_tab,
+k_persistent(const FrameDesc *frames, WorkQueue q, KParams kp, const float *rho_tab,
              const float2 *tw_tab) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item, s_ok;
     for (;;) {
-        if (threadIdx.x == 0) {
-            const int i = atomicAdd(dg.head, 1);
-            int ok = 1;
-            if (i < dg.n) {
-                long long spins = 0;
-                while (ld_acquire(dg.deps + i) > 0) {
-                    if (++spins > dg.spin_limit) {
-                        atomicExch(dg.error, FSE_ETIMEDOUT);
-                        ok = 0;
-                        break;
-                    }
-                    if ((spins & 255) == 0 && *(volatile int *)dg.error) {
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(200);
-                }
-            }
-            s_item = i;
-            s_ok = ok;
-        }
+        if (threadIdx.x == 0) s_item = atomicAdd(q.head, 1);
         __syncthreads();
         const int i = s_item;
-        if (i >= dg.n || !s_ok) break;
+        if (i >= q.n) break;
+        if (threadIdx.x < 32) {
+            const int2 item = q.items[i];
+            const bool ok = wait_area(frames[item.x], item.y, i == q.stuck_item, q);
+            if (threadIdx.x == 0) s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) break;
         float g;
         {
-            const int2 item = dg.items[i];
+            const int2 item = q.items[i];
             const FrameSrc src(frames[item.x], item.y);
             g = run_block<P, false>(src, kp, rho_tab, tw_tab, smem, Trace{nullptr, nullptr, nullptr});
         }
         // Reload the item instead of keeping it live through the iterations.
         asm volatile("" ::: "memory");
-        const int2 item = dg.items[s_item];
+        const int2 item = q.items[s_item];
         const FrameSrc src(frames[item.x], item.y);
         src.store(g);
         write_frame_trace(frames[item.x], item.y, kp, smem);
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int s = dg.succ_ptr[i]; s < dg.succ_ptr[i + 1]; ++s)
-                atomicSub(dg.deps + dg.succ[s], 1);
-        }
+        if (threadIdx.x == 0) st_release_u32(frames[item.x].done + item.y, 1u);
     }
 }
 
@@ -957,17 +984,17 @@ cudaError_t launch_group(const FrameDesc *frames_dev, const int2 *items, int n_i
     });
 }
 
-cudaError_t launch_persistent(const FrameDesc *frames_dev, const DepGraph &dg,
+cudaError_t launch_persistent(const FrameDesc *frames_dev, const WorkQueue &wq,
                               const KParams &kp, const float *rho_tab, const float2 *tw_tab,
                               int precision, int grid, cudaStream_t stream) {
     if (!precision_supported(precision)) return cudaErrorInvalidValue;
     if (precision != FSE_PREC_FP32 && !kp.frags) return cudaErrorInvalidValue;
     cudaError_t e = ensure_attrs(precision);
     if (e != cudaSuccess) return e;
-    if (dg.n <= 0) return cudaSuccess;
+    if (wq.n <= 0) return cudaSuccess;
     return with_precision(precision, [&](auto pc) {
         constexpr int P = decltype(pc)::value;
-        k_persistent<P><<<grid, kThreads, smem_bytes(kp.iters), stream>>>(frames_dev, dg, kp,
+        k_persistent<P><<<grid, kThreads, smem_bytes(kp.iters), stream>>>(frames_dev, wq, kp,
                                                                           rho_tab, tw_tab);
         return cudaGetLastError();
     });

@@ -234,6 +234,7 @@ extern "C" int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_param
     h_desc.bh = bh;
     h_desc.bw = bw;
     h_desc.trace = nullptr;
+    h_desc.done = nullptr;
     h_desc.lb = block_log2(kBlock);
     h_desc.pad0 = 0;
     na_twiddles(h_tw);

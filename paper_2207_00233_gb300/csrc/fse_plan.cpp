@@ -4,9 +4,9 @@
 // Integer-only host code.  The counts N live in a grid padded by one block
 // on every side so that the 8-neighbourhood needs no bounds tests; padding
 // cells hold a sentinel that is never selected and never decremented.
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
-#include <set>
 #include <vector>
 
 #include "../../include/fse.h"
@@ -72,10 +72,10 @@ extern "C" int fse_plan_order(int bw, int bh, const uint8_t *block_lost,
                     if (dy | dx) G.at(by + dy, bx + dx) += 1;  // padding stays very negative
         }
     // Second pass: blocks with nothing to extrapolate are marked -1.  The
-    // others go into buckets by their count, each bucket ordered by raster
-    // index, so that a round visits exactly the blocks with N = N_min in
-    // scan order without rescanning the grid.
-    std::vector<std::set<int>> bucket;
+    // others go into candidate lists by their count.  Counts only decrease,
+    // so a block is appended to each list at most once; entries whose count
+    // has moved on are dropped lazily when their list is used.
+    std::vector<std::vector<int>> bucket(16);
     int pending = 0;
     for (int by = 0; by < bh; ++by)
         for (int bx = 0; bx < bw; ++bx) {
@@ -85,9 +85,7 @@ extern "C" int fse_plan_order(int bw, int bh, const uint8_t *block_lost,
                 group_of_block[b] = -1;
                 continue;
             }
-            const int v = G.at(by, bx);
-            if (v >= (int)bucket.size()) bucket.resize(v + 1);
-            bucket[v].insert(b);
+            bucket[G.at(by, bx)].push_back(b);  // counts are at most 8 + 5
             ++pending;
         }
 
@@ -100,18 +98,25 @@ extern "C" int fse_plan_order(int bw, int bh, const uint8_t *block_lost,
     int32_t g = 0, pos = 0;
     group_ptr[0] = 0;
     std::vector<int> members;
-    int nmin = 0;
     while (pending > 0) {
-        // N_min: smallest count among blocks still to do.  Counts only
-        // decrease, but a decrement can refill a lower bucket, so search
-        // from 0 each round (there are at most 14 buckets).
-        nmin = 0;
-        while (bucket[nmin].empty()) ++nmin;
-        // S: raster scan over the blocks with N_min; a block joins when none
-        // of its neighbours joined before it.  Only the left and the three
-        // upper neighbours can have joined earlier in the scan.
+        // N_min: the smallest count with a live entry.  The live entries of
+        // that list, in raster order, are exactly the blocks with N = N_min.
+        int nmin = 0;
+        for (;; ++nmin) {
+            std::vector<int> &lst = bucket[nmin];
+            size_t k = 0;
+            for (int b : lst)
+                if (G.at(b / bw, b % bw) == nmin) lst[k++] = b;
+            lst.resize(k);
+            if (k) break;
+        }
+        std::vector<int> &cand = bucket[nmin];
+        std::sort(cand.begin(), cand.end());
+        // S: raster scan; a block joins when none of its neighbours joined
+        // before it.  Only the left and the three upper neighbours can have
+        // joined earlier in the scan.
         members.clear();
-        for (int b : bucket[nmin]) {
+        for (int b : cand) {
             const int by = b / bw, bx = b % bw;
             if (s_at(by, bx - 1) | s_at(by - 1, bx - 1) | s_at(by - 1, bx) |
                 s_at(by - 1, bx + 1))
@@ -124,7 +129,6 @@ extern "C" int fse_plan_order(int bw, int bh, const uint8_t *block_lost,
             const int by = b / bw, bx = b % bw;
             block_ids[pos++] = b;
             group_of_block[b] = g;
-            bucket[nmin].erase(b);
             G.at(by, bx) = -1;
             s_at(by, bx) = 0;
             for (int dy = -1; dy <= 1; ++dy)
@@ -134,10 +138,8 @@ extern "C" int fse_plan_order(int bw, int bh, const uint8_t *block_lost,
                     // blocks (-1) and padding keep their value.
                     int &v = G.at(by + dy, bx + dx);
                     if (v >= 0) {
-                        const int nb_idx = (by + dy) * bw + (bx + dx);
-                        bucket[v].erase(nb_idx);
                         --v;
-                        bucket[v].insert(nb_idx);
+                        bucket[v].push_back((by + dy) * bw + (bx + dx));
                     }
                 }
         }

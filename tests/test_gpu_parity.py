@@ -70,6 +70,27 @@ def test_mixed_512(fse, ctx, order, executor):
     assert info["lost_blocks"] == int((o_gob >= 0).sum())
 
 
+@pytest.mark.parametrize("order", [0, 1])
+def test_mixed_512_split_bf16_projection(fse, ctx, order):
+    """The split-BF16 tensor-core projection (about 2e-6 relative error, within
+    the FP32 bound tau): every selection is a valid maximiser within tau and
+    clean blocks match the oracle; it diverges at near-ties more often than
+    the FP32 projection (up to a quarter of the blocks are roots)."""
+    frames = fse_synth.workload_mixed_512()
+    p = fse.make_params(iters=200, rho=0.7, delta=0.2, gamma=0.5, order=order,
+                        executor=fse.FSE_EXEC_PERSISTENT, precision=fse.FSE_PREC_BF16X3)
+    *_, st = run_and_compare(ctx, frames, p, f"512 bf16x3 order {order}", max_root_frac=0.25)
+    print(st)
+
+
+def test_full_size_split_bf16_projection(fse, ctx):
+    frames = fse_synth.workload_batch_1080p(16)
+    p = fse.make_params(iters=200, order=1, executor=fse.FSE_EXEC_PERSISTENT,
+                        precision=fse.FSE_PREC_BF16X3)
+    *_, st = run_and_compare(ctx, frames, p, "1080p bf16x3", sample=(0,), max_root_frac=0.25)
+    print(st)
+
+
 def test_mixed_512_paper_rho(fse, ctx):
     frames = fse_synth.workload_mixed_512()
     p = _params(fse, 200, fse.FSE_ORDER_OPTIMIZED, "persistent", rho=0.8)
