@@ -230,7 +230,7 @@ def precision_sweep(fse, ctx, dev):
     res = {}
     names = [("fp32", fse.FSE_PREC_FP32), ("tf32", fse.FSE_PREC_TF32),
              ("bf16", fse.FSE_PREC_BF16), ("fp16", fse.FSE_PREC_FP16),
-             ("bf16x3", fse.FSE_PREC_BF16X3)]
+             ("bf16x3", fse.FSE_PREC_BF16X3), ("tf32x3", fse.FSE_PREC_TF32X3)]
     for name, prec in names:
         row = {}
         for ex_name, ex in (("persistent", fse.FSE_EXEC_PERSISTENT), ("groups", fse.FSE_EXEC_GROUPS)):

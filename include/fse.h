@@ -69,6 +69,7 @@ extern "C" {
 #define FSE_PREC_BF16 2
 #define FSE_PREC_FP16 3
 #define FSE_PREC_BF16X3 4      /* split-BF16 operands (hi*hi + hi*lo + lo*hi) */
+#define FSE_PREC_TF32X3 5      /* split-TF32 operands, FP32-grade accuracy    */
 
 /* How the groups are dispatched on the device. */
 #define FSE_EXEC_GROUPS 0      /* one launch per group (plain path)              */

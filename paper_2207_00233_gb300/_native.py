@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libfse_gb300.so")
 FSE_OK, FSE_EINVAL, FSE_ENOMEM, FSE_EAGAIN, FSE_ETIMEDOUT, FSE_ECUDA, FSE_ENOTFOUND = range(7)
 FSE_ETOOBIG = 7
 FSE_ORDER_LINESCAN, FSE_ORDER_OPTIMIZED = 0, 1
-FSE_PREC_FP32, FSE_PREC_TF32, FSE_PREC_BF16, FSE_PREC_FP16, FSE_PREC_BF16X3 = range(5)
+FSE_PREC_FP32, FSE_PREC_TF32, FSE_PREC_BF16, FSE_PREC_FP16, FSE_PREC_BF16X3, FSE_PREC_TF32X3 = range(6)
 FSE_EXEC_GROUPS, FSE_EXEC_PERSISTENT = 0, 1
 FSE_MAX_ITERS = 1024
 

@@ -151,7 +151,7 @@ const float *fse_ctx::rho_table(float rho, int block, int *rc) {
 const uint4 *fse_ctx::frag_table(int precision, int *rc) {
     *rc = FSE_OK;
     if (precision == FSE_PREC_FP32) return nullptr;
-    if (precision < 0 || precision > 4) {
+    if (precision < 0 || precision > 5) {
         *rc = FSE_EINVAL;
         return nullptr;
     }

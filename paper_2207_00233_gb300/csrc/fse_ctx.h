@@ -78,7 +78,7 @@ struct fse_ctx {
 
     fse::DevBuf tw_dev;                                   // 64 twiddles
     std::vector<std::pair<float, fse::DevBuf>> rho_tabs;  // Eq. (2) decay per (rho, block)
-    fse::DevBuf frags[5];                                 // per precision (tensor cores)
+    fse::DevBuf frags[6];                                 // per precision (tensor cores)
     fse::Workspace ws;  // synchronous API
     std::mutex api_mu;  // one synchronous API call at a time
     std::mutex mem_mu;  // budget accounting and table cache

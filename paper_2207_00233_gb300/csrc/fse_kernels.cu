@@ -279,9 +279,17 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1
 // Per precision: K per mma instruction, and the operand registers of one
 // fragment (x3 precisions carry a low part as well).
 template <int P> struct Prec {
-    static constexpr int kStep = (P == FSE_PREC_TF32) ? 8 : 16;
-    static constexpr bool kSplit = (P == FSE_PREC_BF16X3);
+    static constexpr bool kTf32 = (P == FSE_PREC_TF32 || P == FSE_PREC_TF32X3);
+    static constexpr int kStep = kTf32 ? 8 : 16;
+    static constexpr bool kSplit = (P == FSE_PREC_BF16X3 || P == FSE_PREC_TF32X3);
 };
+
+// TF32 operand and, for the split type, the TF32 remainder.
+template <int P>
+__device__ __forceinline__ void cv_tf32_pair(float v, uint32_t &h, uint32_t &l) {
+    h = cv_tf32(v);
+    if (P == FSE_PREC_TF32X3) l = cv_tf32(v - __uint_as_float(h));
+}
 
 // An operand fragment: the 4 (A) or 2 (B) registers, plus the low parts.
 struct FragA { uint32_t h[4], l[4]; };
@@ -304,11 +312,11 @@ template <int P, class FA>
 __device__ __forceinline__ FragA load_a(FA A, int r0, int k0) {
     const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
     FragA f;
-    if (P == FSE_PREC_TF32) {
-        f.h[0] = cv_tf32(A(r0 + g, k0 + t));
-        f.h[1] = cv_tf32(A(r0 + g + 8, k0 + t));
-        f.h[2] = cv_tf32(A(r0 + g, k0 + t + 4));
-        f.h[3] = cv_tf32(A(r0 + g + 8, k0 + t + 4));
+    if (Prec<P>::kTf32) {
+        cv_tf32_pair<P>(A(r0 + g, k0 + t), f.h[0], f.l[0]);
+        cv_tf32_pair<P>(A(r0 + g + 8, k0 + t), f.h[1], f.l[1]);
+        cv_tf32_pair<P>(A(r0 + g, k0 + t + 4), f.h[2], f.l[2]);
+        cv_tf32_pair<P>(A(r0 + g + 8, k0 + t + 4), f.h[3], f.l[3]);
     } else {
         pack_pair<P>(A(r0 + g, k0 + 2 * t), A(r0 + g, k0 + 2 * t + 1), f.h[0], f.l[0]);
         pack_pair<P>(A(r0 + g + 8, k0 + 2 * t), A(r0 + g + 8, k0 + 2 * t + 1), f.h[1], f.l[1]);
@@ -324,9 +332,9 @@ template <int P, class FB>
 __device__ __forceinline__ FragB load_b(FB B, int k0, int c0) {
     const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
     FragB f;
-    if (P == FSE_PREC_TF32) {
-        f.h[0] = cv_tf32(B(k0 + t, c0 + g));
-        f.h[1] = cv_tf32(B(k0 + t + 4, c0 + g));
+    if (Prec<P>::kTf32) {
+        cv_tf32_pair<P>(B(k0 + t, c0 + g), f.h[0], f.l[0]);
+        cv_tf32_pair<P>(B(k0 + t + 4, c0 + g), f.h[1], f.l[1]);
     } else {
         pack_pair<P>(B(k0 + 2 * t, c0 + g), B(k0 + 2 * t + 1, c0 + g), f.h[0], f.l[0]);
         pack_pair<P>(B(k0 + 2 * t + 8, c0 + g), B(k0 + 2 * t + 9, c0 + g), f.h[1], f.l[1]);
@@ -336,8 +344,12 @@ __device__ __forceinline__ FragB load_b(FB B, int k0, int c0) {
 
 template <int P>
 __device__ __forceinline__ void mma_step(float (&d)[4], const FragA &a, const FragB &b) {
-    if (P == FSE_PREC_TF32) {
+    if (Prec<P>::kTf32) {
         mma_tf32(d, a.h[0], a.h[1], a.h[2], a.h[3], b.h[0], b.h[1]);
+        if (P == FSE_PREC_TF32X3) {
+            mma_tf32(d, a.h[0], a.h[1], a.h[2], a.h[3], b.l[0], b.l[1]);
+            mma_tf32(d, a.l[0], a.l[1], a.l[2], a.l[3], b.h[0], b.h[1]);
+        }
     } else if (P == FSE_PREC_FP16) {
         mma_f16(d, a.h[0], a.h[1], a.h[2], a.h[3], b.h[0], b.h[1]);
     } else {
@@ -898,14 +910,15 @@ static cudaError_t with_precision(int precision, F f) {
     case FSE_PREC_BF16: return f(std::integral_constant<int, FSE_PREC_BF16>());
     case FSE_PREC_FP16: return f(std::integral_constant<int, FSE_PREC_FP16>());
     case FSE_PREC_BF16X3: return f(std::integral_constant<int, FSE_PREC_BF16X3>());
+    case FSE_PREC_TF32X3: return f(std::integral_constant<int, FSE_PREC_TF32X3>());
     default: return cudaErrorInvalidValue;
     }
 }
 
-static bool g_attr_done[5] = {false, false, false, false, false};
+static bool g_attr_done[6] = {false, false, false, false, false, false};
 
 static cudaError_t ensure_attrs(int precision) {
-    if (precision < 0 || precision > 4) return cudaErrorInvalidValue;
+    if (precision < 0 || precision > 5) return cudaErrorInvalidValue;
     if (g_attr_done[precision]) return cudaSuccess;
     const int max_smem = smem_bytes(FSE_MAX_ITERS);
     cudaError_t e = with_precision(precision, [&](auto pc) {
@@ -923,7 +936,7 @@ static cudaError_t ensure_attrs(int precision) {
     return e;
 }
 
-bool precision_supported(int precision) { return precision >= 0 && precision <= 4; }
+bool precision_supported(int precision) { return precision >= 0 && precision <= 5; }
 
 size_t frag_bytes(int precision) {
     size_t n = 0;

@@ -71,6 +71,25 @@ def test_mixed_512(fse, ctx, order, executor):
 
 
 @pytest.mark.parametrize("order", [0, 1])
+def test_mixed_512_split_tf32_projection(fse, ctx, order):
+    """The split-TF32 tensor-core projection is FP32-grade: the same parity
+    criteria as the FP32 path."""
+    frames = fse_synth.workload_mixed_512()
+    p = fse.make_params(iters=200, rho=0.7, delta=0.2, gamma=0.5, order=order,
+                        executor=fse.FSE_EXEC_PERSISTENT, precision=fse.FSE_PREC_TF32X3)
+    *_, st = run_and_compare(ctx, frames, p, f"512 tf32x3 order {order}")
+    print(st)
+
+
+def test_full_size_split_tf32_projection(fse, ctx):
+    frames = fse_synth.workload_batch_1080p(16)
+    p = fse.make_params(iters=200, order=1, executor=fse.FSE_EXEC_PERSISTENT,
+                        precision=fse.FSE_PREC_TF32X3)
+    *_, st = run_and_compare(ctx, frames, p, "1080p tf32x3", sample=(0, 5))
+    print(st)
+
+
+@pytest.mark.parametrize("order", [0, 1])
 def test_mixed_512_split_bf16_projection(fse, ctx, order):
     """The split-BF16 tensor-core projection (about 2e-6 relative error, within
     the FP32 bound tau): every selection is a valid maximiser within tau and

@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 # unit roundoff of the operands (8-bit bf16, 11-bit fp16 / tf32 mantissas;
 # split bf16 keeps about 16 bits)
 U = {"tf32": 2.0 ** -11, "bf16": 2.0 ** -8, "fp16": 2.0 ** -11, "bf16x3": 2.0 ** -16,
-     "fp32": 2.0 ** -22}
+     "tf32x3": 2.0 ** -21, "fp32": 2.0 ** -22}
 
 
 @pytest.fixture(scope="module")
@@ -39,7 +39,8 @@ def ctx(fse):
 
 def _prec(fse, name):
     return {"fp32": fse.FSE_PREC_FP32, "tf32": fse.FSE_PREC_TF32, "bf16": fse.FSE_PREC_BF16,
-            "fp16": fse.FSE_PREC_FP16, "bf16x3": fse.FSE_PREC_BF16X3}[name]
+            "fp16": fse.FSE_PREC_FP16, "bf16x3": fse.FSE_PREC_BF16X3,
+            "tf32x3": fse.FSE_PREC_TF32X3}[name]
 
 
 def _areas(n):
@@ -51,7 +52,7 @@ def _areas(n):
     return f, cls
 
 
-@pytest.mark.parametrize("name", ["fp32", "tf32", "bf16", "fp16", "bf16x3"])
+@pytest.mark.parametrize("name", ["fp32", "tf32", "bf16", "fp16", "bf16x3", "tf32x3"])
 def test_projection_error_within_operand_precision(fse, ctx, name):
     import torch
     dev = torch.device("cuda:0")
@@ -70,7 +71,7 @@ def test_projection_error_within_operand_precision(fse, ctx, name):
         assert rel <= 4 * U[name], (name, i, rel)
 
 
-@pytest.mark.parametrize("name", ["tf32", "bf16", "fp16", "bf16x3"])
+@pytest.mark.parametrize("name", ["tf32", "bf16", "fp16", "bf16x3", "tf32x3"])
 def test_update_consistent_with_its_spectra(fse, ctx, name):
     """Whatever the projection precision, K iterations leave the residual
     equal to DFT{w (f - g)} up to the projection error."""
@@ -101,7 +102,7 @@ def test_update_consistent_with_its_spectra(fse, ctx, name):
         assert np.abs(rg - spatial).max() <= (8 * U[name] + 2e-4) * scale, (name, i)
 
 
-@pytest.mark.parametrize("name", ["tf32", "bf16", "fp16", "bf16x3"])
+@pytest.mark.parametrize("name", ["tf32", "bf16", "fp16", "bf16x3", "tf32x3"])
 def test_frame_quality_matches_oracle(fse, ctx, name):
     """512x512 mixed losses, K = 200: the reduced-precision projection
     conceals as well as the FP64 oracle against the ground truth (within
