@@ -11,6 +11,8 @@
 #include <thread>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include "../../include/fse.h"
@@ -18,6 +20,57 @@
 #include "fse_internal.h"
 
 using namespace fse;
+
+// ---------------------------------------------------------------------------
+// TMA descriptors of a frame
+// ---------------------------------------------------------------------------
+
+// cuTensorMapEncodeTiled from the driver, through the runtime (no link
+// dependency on libcuda); null when the driver does not provide it.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+// One 2-D map with a kStageCols x kStageRows box; samples outside the frame
+// read as zero.
+static bool encode_map(CUtensorMap *map, CUtensorMapDataType type, const void *base,
+                       int width, int height, size_t row_bytes) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || !base || (reinterpret_cast<uintptr_t>(base) & 15) || (row_bytes & 15))
+        return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)height};
+    const cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+    const cuuint32_t box[2] = {(cuuint32_t)kStageCols, (cuuint32_t)kStageRows};
+    const cuuint32_t elem[2] = {1, 1};
+    return enc(map, type, 2, const_cast<void *>(base), dims, strides, box, elem,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The luma, loss-mask and working-frame maps of a frame.  False when a
+// buffer or row pitch is not 16-byte aligned (the frame is then gathered
+// with plain loads).
+static bool encode_frame_maps(const FrameDesc &d, CUtensorMap *maps) {
+    static_assert(sizeof(CUtensorMap) == kTensorMapBytes, "tensor map size");
+    return encode_map(&maps[0], CU_TENSOR_MAP_DATA_TYPE_UINT8, d.luma, d.W, d.H,
+                      (size_t)d.stride) &&
+           encode_map(&maps[1], CU_TENSOR_MAP_DATA_TYPE_UINT8, d.mask, d.W, d.H,
+                      (size_t)d.stride) &&
+           encode_map(&maps[2], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, d.work, d.W, d.H,
+                      (size_t)d.wstride * sizeof(float));
+}
 
 // ---------------------------------------------------------------------------
 // Tables
@@ -248,6 +301,7 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
         d.wstride = (d.W + 31) & ~31;
         d.lb = block_log2(p->block);
         d.pad0 = 0;
+        d.tmaps = nullptr;
         d.bh = (d.H + p->block - 1) / p->block;
         d.bw = (d.W + p->block - 1) / p->block;
         lost_off[i + 1] = lost_off[i] + d.bh * d.bw;
@@ -385,8 +439,18 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
         uint32_t *dp = static_cast<uint32_t *>(ws.done.ptr);
         for (int i = 0; i < n; ++i) fd[i].done = persistent ? dp + lost_off[i] : nullptr;
     }
+    // TMA descriptors (frames whose buffers allow it)
+    std::vector<CUtensorMap> maps((size_t)kMapsPerFrame * n);
+    if (n_items > 0) {
+        rc = ctx->dev_reserve(ws.tmaps, sizeof(CUtensorMap) * kMapsPerFrame * n);
+        if (rc) return rc;
+        const char *mp = static_cast<const char *>(ws.tmaps.ptr);
+        for (int i = 0; i < n; ++i)
+            if (encode_frame_maps(fd[i], &maps[(size_t)kMapsPerFrame * i]))
+                fd[i].tmaps = mp + sizeof(CUtensorMap) * kMapsPerFrame * i;
+    }
     const size_t stage_bytes = sizeof(FrameDesc) * n + sizeof(int32_t) * nblocks +
-                               sizeof(int2) * n_items + 256;
+                               sizeof(int2) * n_items + sizeof(CUtensorMap) * maps.size() + 256;
     rc = ctx->host_reserve(ws.stage, stage_bytes);
     if (rc) return rc;
     char *st = static_cast<char *>(ws.stage.ptr);
@@ -404,6 +468,7 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
     rc = put(ws.frames.ptr, fd.data(), sizeof(FrameDesc) * n);
     if (!rc) rc = put(ws.gob.ptr, gob_h.data(), sizeof(int32_t) * nblocks);
     if (!rc) rc = put(ws.items.ptr, items.data(), sizeof(int2) * n_items);
+    if (!rc && n_items > 0) rc = put(ws.tmaps.ptr, maps.data(), sizeof(CUtensorMap) * maps.size());
     if (rc) return rc;
     if (persistent && nblocks > 0)
         CK(cudaMemsetAsync(ws.done.ptr, 0, sizeof(uint32_t) * nblocks, stream));
@@ -419,7 +484,9 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
     }
 
     // ---- extrapolation ----
-    const KParams kp{p->rho, p->delta, p->gamma, p->iters, frags, block_log2(p->block)};
+    int *status = static_cast<int *>(ws.status.ptr);
+    const KParams kp{p->rho, p->delta, p->gamma, p->iters, frags, block_log2(p->block),
+                     status + 1};
     const FrameDesc *fdev = static_cast<const FrameDesc *>(ws.frames.ptr);
     const float2 *tw_tab = static_cast<const float2 *>(ctx->tw_dev.ptr);
     int launches = 1;  // block-loss map
@@ -429,10 +496,9 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
             CK(cudaEventCreate(&ws.k_begin));
             CK(cudaEventCreate(&ws.k_end));
         }
+        CK(cudaMemsetAsync(status, 0, sizeof(int) * 2, stream));
         CK(cudaEventRecord(ws.k_begin, stream));
         if (persistent) {
-            int *status = static_cast<int *>(ws.status.ptr);
-            CK(cudaMemsetAsync(status, 0, sizeof(int) * 2, stream));
             WorkQueue wq;
             wq.items = static_cast<const int2 *>(ws.items.ptr);
             wq.head = status;
@@ -444,7 +510,6 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
             if (ctx->persistent_ctas > 0) per_sm = std::min(per_sm, ctx->persistent_ctas);
             const int grid = std::min<int>((int)n_items, ctx->num_sms * per_sm);
             CK(launch_persistent(fdev, wq, kp, rho_tab, tw_tab, p->precision, grid, stream));
-            ws.status_live = true;
             launches += 1;
         } else {
             const int2 *idev = static_cast<const int2 *>(ws.items.ptr);
@@ -457,6 +522,7 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
         }
         CK(cudaEventRecord(ws.k_end, stream));
         ws.k_timed = true;
+        ws.status_live = true;
     }
     ws.lost_blocks = lost_blocks;
     ws.groups = max_groups;
@@ -480,7 +546,7 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
     return FSE_OK;
 }
 
-// Reads the status word of the last persistent launch (after a sync).
+// Reads the status word of the last launch (after a sync).
 int fse::read_status(fse_ctx *, Workspace &ws, cudaStream_t stream) {
     if (!ws.status_live) return FSE_OK;
     int err = 0;
@@ -503,6 +569,7 @@ void fse::release_workspace(fse_ctx *ctx, Workspace &ws) {
     ctx->dev_release(ws.items);
     ctx->dev_release(ws.done);
     ctx->dev_release(ws.status);
+    ctx->dev_release(ws.tmaps);
     ctx->dev_release(ws.trace);
     ctx->dev_release(ws.d_luma);
     ctx->dev_release(ws.d_mask);
@@ -598,8 +665,10 @@ extern "C" int fse_conceal_batch_host(fse_ctx *ctx, const fse_frame *frames, int
     Workspace &ws = ctx->ws;
     size_t total = 0;
     std::vector<size_t> off(n + 1, 0);
+    // device rows are padded to 16 bytes (TMA row pitch)
+    auto pitch = [&](int i) { return (frames[i].width + 15) & ~15; };
     for (int i = 0; i < n; ++i) {
-        off[i + 1] = off[i] + (((size_t)frames[i].height * frames[i].width + 255) & ~(size_t)255);
+        off[i + 1] = off[i] + (((size_t)frames[i].height * pitch(i) + 255) & ~(size_t)255);
     }
     total = off[n];
     rc = ctx->dev_reserve(ws.d_luma, total);
@@ -612,11 +681,11 @@ extern "C" int fse_conceal_batch_host(fse_ctx *ctx, const fse_frame *frames, int
         uint8_t *dl = static_cast<uint8_t *>(ws.d_luma.ptr) + off[i];
         uint8_t *dm = static_cast<uint8_t *>(ws.d_mask.ptr) + off[i];
         uint8_t *dout = static_cast<uint8_t *>(ws.d_out.ptr) + off[i];
-        CK(cudaMemcpy2DAsync(dl, h.width, h.luma, h.stride, h.width, h.height,
+        CK(cudaMemcpy2DAsync(dl, pitch(i), h.luma, h.stride, h.width, h.height,
                              cudaMemcpyHostToDevice, stream));
-        CK(cudaMemcpy2DAsync(dm, h.width, h.loss_mask, h.stride, h.width, h.height,
+        CK(cudaMemcpy2DAsync(dm, pitch(i), h.loss_mask, h.stride, h.width, h.height,
                              cudaMemcpyHostToDevice, stream));
-        dev[i] = fse_frame{dl, dout, dm, h.width, h.height, h.width};
+        dev[i] = fse_frame{dl, dout, dm, h.width, h.height, pitch(i)};
     }
     rc = run_batch(ctx, ws, dev.data(), n, params, stream, nullptr);
     ctx->last_lost_blocks = ws.lost_blocks;
@@ -625,7 +694,7 @@ extern "C" int fse_conceal_batch_host(fse_ctx *ctx, const fse_frame *frames, int
     if (rc) return rc;
     for (int i = 0; i < n; ++i) {
         const fse_frame &h = frames[i];
-        CK(cudaMemcpy2DAsync(h.out, h.stride, dev[i].out, h.width, h.width, h.height,
+        CK(cudaMemcpy2DAsync(h.out, h.stride, dev[i].out, dev[i].stride, h.width, h.height,
                              cudaMemcpyDeviceToHost, stream));
     }
     CK(cudaStreamSynchronize(stream));

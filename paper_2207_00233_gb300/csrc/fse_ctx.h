@@ -28,13 +28,14 @@ struct HostBuf {
 // Everything one in-flight batch needs on the device.
 struct Workspace {
     DevBuf frames, work, lost, lost_off, gob, items, done, status, trace;
+    DevBuf tmaps;                  // TMA descriptors of the frames (3 per frame)
     DevBuf d_luma, d_mask, d_out;  // device copies of host frames
     HostBuf stage;                 // pinned staging for uploads / readback
     HostBuf io;                    // pinned staging of serving frames
     cudaEvent_t staged = nullptr;  // uploads from `stage` are complete
     cudaEvent_t k_begin = nullptr, k_end = nullptr;  // around the extrapolation
     bool k_timed = false;
-    bool status_live = false;      // status word of a persistent launch pending
+    bool status_live = false;      // status word of the last launch pending
     int lost_blocks = 0, groups = 0, launches = 0;  // of the last batch
     std::vector<int16_t *> trace_ptr;               // per frame of the last batch
     std::vector<size_t> trace_len;

@@ -31,6 +31,10 @@ constexpr int kTwOff = kW4Bytes;                       // 64 x float2
 constexpr int kRedOff = kTwOff + kDft * 8;             // reduction scratch
 constexpr int kRedBytes = 8 * 4 + 8 * 16 + 64;         // smax[8], cand[8], misc
 constexpr int kListOff = kRedOff + kRedBytes;          // dc list, then u list
+// misc[2..3]: TMA mbarrier, misc[4]: its next phase parity, misc[5..6]: the
+// persistent executor's claimed item and wait result
+constexpr int kMbarOff = kRedOff + 8 * 4 + 8 * 16 + 8;
+static_assert(kMbarOff % 8 == 0 && kMbarOff + 20 <= kListOff, "mbarrier placement");
 inline int smem_bytes(int iters) {
     return kListOff + iters * 8 + ((iters * 2 + 15) / 16) * 16;
 }
@@ -57,6 +61,8 @@ struct KParams {
     const uint4 *frags;  // packed DFT operand fragments of the tensor-core
                          // projection (null for FSE_PREC_FP32)
     int lb;              // log2 of the block size B; the area is (B + 32)^2
+    int *error;          // status word for a failed TMA wait (group launches;
+                         // null: frames are gathered with plain loads)
 };
 
 // Block sizes: B = 16 (the 48x48 area fills the tile) or B = 8, 4, 2 with the
@@ -77,6 +83,24 @@ constexpr int kYStride = kYCols + 4;        // conflict-free fragment loads
 constexpr int kYOff = 2 * kArea * kTileStride * 4;                 // after the tiles
 constexpr int kR0Off = kYOff + kYRows * kYStride * 4;              // 64 x 33 float2
 static_assert(kR0Off + kDft * kHalfCols * 8 <= kW4Bytes, "projection scratch overflow");
+
+// TMA staging of a frame area, before the gather: the luma, loss-mask and
+// working-frame tiles of 48 x 48 samples, starting at the sample row of the
+// area and at the 16-byte boundary at or below its first column (the copy
+// must start on a 16-byte boundary).  With the 16-sample frame the area's
+// first column is at most 14 samples past that boundary and M = B + 32
+// <= 34 + 14 for B < 16, so 48 columns always cover it.  The tiles share the
+// (not yet used) projection scratch at kYOff.
+constexpr int kStageCols = 48, kStageRows = 48;
+constexpr int kStageLumaOff = kYOff;
+constexpr int kStageMaskOff = kStageLumaOff + kStageCols * kStageRows;
+constexpr int kStageWorkOff = kStageMaskOff + kStageCols * kStageRows;
+constexpr int kStageBytes = kStageCols * kStageRows * (1 + 1 + 4);  // 13824
+static_assert(kStageLumaOff % 128 == 0 && kStageMaskOff % 128 == 0 && kStageWorkOff % 128 == 0,
+              "TMA destinations must be 128-byte aligned");
+static_assert(kStageWorkOff + kStageCols * kStageRows * 4 <= kW4Bytes, "staging overflow");
+constexpr int kTensorMapBytes = 128;       // one CUtensorMap
+constexpr int kMapsPerFrame = 3;           // luma, mask, working frame
 size_t frag_bytes(int precision);
 cudaError_t launch_build_frags(int precision, const float2 *tw, uint4 *out,
                                cudaStream_t stream);
@@ -93,6 +117,8 @@ struct FrameDesc {
     uint32_t *done;          // [bh*bw] completion flags (persistent executor)
     int lb;                  // log2 of the block size B (1..4)
     int pad0;
+    const void *tmaps;       // 3 tensor maps (luma, mask, work), 64-byte
+                             // aligned, or null: gather with plain loads
 };
 
 // Work of the persistent executor: items are (frame, block) pairs in group

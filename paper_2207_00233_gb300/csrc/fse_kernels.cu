@@ -65,6 +65,56 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// ---- TMA: bulk tensor copies completed on a shared-memory mbarrier ----------
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Waits for the phase with the given parity to complete; gives up after
+// `limit_ns` nanoseconds.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          unsigned long long limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+// 2-D tiled load of the box at (x, y) of `map` (x: innermost, in elements;
+// out-of-range samples read as 0) into shared memory at `dst`.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *map, int x, int y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+// A TMA copy that has not completed after this long is reported as an error.
+constexpr unsigned long long kStageLimitNs = 2000000000ull;
+
 // ---- sources: where an area comes from and where its result goes -----------
 
 // A block of a frame in a batch.  Classes follow Sec. 2: a lost sample of a
@@ -73,20 +123,62 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
 struct FrameSrc {
     const FrameDesc &fd;
     int by, bx, self, gself;
+    const unsigned char *stage;  // TMA-staged tiles of the area, or null
 
-    __device__ FrameSrc(const FrameDesc &f, int block)
-        : fd(f), by(block / f.bw), bx(block % f.bw), self(block), gself(f.gob[block]) {}
+    __device__ FrameSrc(const FrameDesc &f, int block, const unsigned char *st = nullptr)
+        : fd(f), by(block / f.bw), bx(block % f.bw), self(block), gself(f.gob[block]),
+          stage(st) {}
+
+    // Class and weight of area sample (m, n) at frame position (y, x), given
+    // its loss flag, luma and working-frame value.
+    __device__ __forceinline__ void classify(int y, int x, bool lost, float luma, float work,
+                                             float rho, float delta, float &w, float &v) const {
+        if (!lost) {
+            w = rho;
+            v = luma;
+        } else {
+            const int cb = (y >> fd.lb) * fd.bw + (x >> fd.lb);
+            if (cb != self) {
+                const int gc = fd.gob[cb];
+                if (gc >= 0 && gc < gself) {
+                    w = delta * rho;
+                    v = work;
+                }
+            }
+        }
+    }
 
     __device__ void gather(float *xt, float *wt, const float *rho_tab, float delta) const {
         const int B = 1 << fd.lb, M = B + 2 * kBorder;
         const int y0 = by * B - kBorder, x0 = bx * B - kBorder;
+        if (stage) {
+            // tiles start at column x0 rounded down to a multiple of 16
+            const int dx = x0 - (x0 & ~15);
+            const uint8_t *sl = stage;
+            const uint8_t *sm = stage + (kStageMaskOff - kStageLumaOff);
+            const float *sw = reinterpret_cast<const float *>(stage + (kStageWorkOff - kStageLumaOff));
+            for (int p = threadIdx.x; p < kArea * kArea; p += kThreads) {
+                const int m = p / kArea, n = p - m * kArea;
+                const int y = y0 + m, x = x0 + n;
+                float w = 0.f, v = 0.f;
+                if (m < M && n < M && y >= 0 && y < fd.H && x >= 0 && x < fd.W) {
+                    const int q = m * kStageCols + n + dx;
+                    const bool lost = sm[q] != 0;
+                    classify(y, x, lost, (float)sl[q], lost ? sw[q] : 0.f, rho_tab[p], delta, w, v);
+                }
+                xt[m * kTileStride + n] = w * v;
+                wt[m * kTileStride + n] = w;
+            }
+            return;
+        }
         for (int p = threadIdx.x; p < kArea * kArea; p += kThreads) {
             const int m = p / kArea, n = p - m * kArea;
             const int y = y0 + m, x = x0 + n;
             float w = 0.f, v = 0.f;
             if (m < M && n < M && y >= 0 && y < fd.H && x >= 0 && x < fd.W) {
                 const size_t q = (size_t)y * fd.stride + x;
-                if (!fd.mask[q]) {
+                const bool lost = fd.mask[q] != 0;
+                if (!lost) {
                     w = rho_tab[p];
                     v = (float)fd.luma[q];
                 } else {
@@ -116,6 +208,8 @@ struct FrameSrc {
         const float v = fminf(fmaxf(g, 0.f), 255.f);
         fd.work[(size_t)y * fd.wstride + x] = v;
         fd.out[q] = (uint8_t)__float2int_rn(v);
+        // later blocks read this sample with TMA (async proxy)
+        asm volatile("fence.proxy.async.global;" ::: "memory");
     }
 };
 
@@ -763,15 +857,69 @@ __device__ __forceinline__ void write_frame_trace(const FrameDesc &fd, int block
         t[it] = (W0 > 0.f) ? (int16_t)ul[it] : (int16_t)-1;
 }
 
+// The CTA's staging mbarrier and the parity of its next phase (shared, so
+// that no register carries it through the iterations).
+__device__ __forceinline__ void stage_init(unsigned char *smem) {
+    if (threadIdx.x == 0) {
+        mbar_init(smem_addr(smem + kMbarOff), 1);
+        *reinterpret_cast<uint32_t *>(smem + kMbarOff + 8) = 0u;
+    }
+}
+
+// Stages the luma, mask and working-frame tiles of the area of `block` with
+// three TMA copies completing on the CTA's mbarrier.  Returns false on every
+// thread when the copies did not complete within kStageLimitNs; the caller
+// then leaves the kernel.
+__device__ __forceinline__ bool stage_area(const FrameDesc &fd, int block, unsigned char *smem) {
+    const uint32_t bar = smem_addr(smem + kMbarOff);
+    volatile uint32_t *phase = reinterpret_cast<volatile uint32_t *>(smem + kMbarOff + 8);
+    const uint32_t ph = *phase;
+    if (threadIdx.x == 0) {
+        const int B = 1 << fd.lb, by = block / fd.bw, bx = block - by * fd.bw;
+        const int y0 = by * B - kBorder, xs = (bx * B - kBorder) & ~15;
+        const unsigned char *maps = static_cast<const unsigned char *>(fd.tmaps);
+        // Order the CTA's earlier accesses to the staging region (previous
+        // block) and the frame samples published by earlier blocks before
+        // the copies.
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        mbar_arrive_expect_tx(bar, kStageBytes);
+        tma_load_2d(smem_addr(smem + kStageLumaOff), maps, xs, y0, bar);
+        tma_load_2d(smem_addr(smem + kStageMaskOff), maps + kTensorMapBytes, xs, y0, bar);
+        tma_load_2d(smem_addr(smem + kStageWorkOff), maps + 2 * kTensorMapBytes, xs, y0, bar);
+    }
+    const bool ok = __syncthreads_and(mbar_wait(bar, ph, kStageLimitNs));
+    if (!ok) mbar_wait(bar, ph, kStageLimitNs);  // copies in flight land before leaving
+    if (threadIdx.x == 0) *phase = ph ^ 1u;      // every thread has read it
+    return ok;
+}
+
+// Shared memory of the block kernels starts 128-byte aligned (TMA
+// destinations); checked at run time, frames fall back to plain loads if not.
+__device__ __forceinline__ bool stage_capable(const unsigned char *smem) {
+    return (smem_addr(smem) & 127u) == 0;
+}
+
 template <int P>
 __global__ void __launch_bounds__(kThreads, 3)
 k_group(const FrameDesc *frames, const int2 *items, KParams kp, const float *rho_tab,
         const float2 *tw_tab) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     float g;
     {
         const int2 item = items[blockIdx.x];
-        const FrameSrc src(frames[item.x], item.y);
+        const FrameDesc &fd = frames[item.x];
+        const unsigned char *stage = nullptr;
+        if (fd.tmaps && kp.error && stage_capable(smem)) {
+            stage_init(smem);
+            __syncthreads();
+            if (!stage_area(fd, item.y, smem)) {
+                if (threadIdx.x == 0) atomicExch(kp.error, FSE_ETIMEDOUT);
+                return;
+            }
+            stage = smem + kStageLumaOff;
+        }
+        const FrameSrc src(fd, item.y, stage);
         g = run_block<P, false>(src, kp, rho_tab, tw_tab, smem, Trace{nullptr, nullptr, nullptr});
     }
     // Reload the item instead of keeping it live through the iterations.
@@ -835,8 +983,12 @@ template <int P>
 __global__ void __launch_bounds__(kThreads, 3)
 k_persistent(const FrameDesc *frames, WorkQueue q, KParams kp, const float *rho_tab,
              const float2 *tw_tab) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_item, s_ok;
+    extern __shared__ __align__(128) unsigned char smem[];
+    // claimed item and wait result, beside the mbarrier (no static shared
+    // memory, so that the dynamic region starts at the window's base)
+    int &s_item = *reinterpret_cast<int *>(smem + kMbarOff + 12);
+    int &s_ok = *reinterpret_cast<int *>(smem + kMbarOff + 16);
+    if (stage_capable(smem)) stage_init(smem);  // made visible by the first barrier below
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(q.head, 1);
         __syncthreads();
@@ -852,7 +1004,16 @@ k_persistent(const FrameDesc *frames, WorkQueue q, KParams kp, const float *rho_
         float g;
         {
             const int2 item = q.items[i];
-            const FrameSrc src(frames[item.x], item.y);
+            const FrameDesc &fd = frames[item.x];
+            const unsigned char *stage = nullptr;
+            if (fd.tmaps && stage_capable(smem)) {
+                if (!stage_area(fd, item.y, smem)) {
+                    if (threadIdx.x == 0) atomicExch(q.error, FSE_ETIMEDOUT);
+                    break;
+                }
+                stage = smem + kStageLumaOff;
+            }
+            const FrameSrc src(fd, item.y, stage);
             g = run_block<P, false>(src, kp, rho_tab, tw_tab, smem, Trace{nullptr, nullptr, nullptr});
         }
         // Reload the item instead of keeping it live through the iterations.
@@ -871,7 +1032,7 @@ template <int P>
 __global__ void __launch_bounds__(kThreads, 3)
 k_areas(const float *area_f, const uint8_t *area_cls, KParams kp, const float *rho_tab,
         const float2 *tw_tab, float *g_out, int32_t *u_out, float *dc_out, float *r_out) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const size_t a = blockIdx.x;
     const AreaSrc src{area_f + a * kArea * kArea, area_cls + a * kArea * kArea,
                       g_out + a * kBlock * kBlock, kp.lb};

@@ -237,6 +237,7 @@ extern "C" int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_param
     h_desc.done = nullptr;
     h_desc.lb = block_log2(kBlock);
     h_desc.pad0 = 0;
+    h_desc.tmaps = nullptr;  // plain-load gather
     na_twiddles(h_tw);
     const double cm = 0.5 * (kArea - 1);
     for (int m = 0; m < kArea; ++m)

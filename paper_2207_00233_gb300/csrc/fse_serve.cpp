@@ -32,8 +32,11 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
     return std::chrono::duration<double, std::milli>(b - a).count();
 }
 
+// Device rows are padded to 16 bytes (TMA row pitch).
+int device_pitch(const fse_frame &f) { return (f.width + 15) & ~15; }
+
 size_t frame_bytes(const fse_frame &f) {
-    return ((size_t)f.width * f.height + 255) & ~(size_t)255;
+    return ((size_t)device_pitch(f) * f.height + 255) & ~(size_t)255;
 }
 
 // Block-loss map of a host frame.
@@ -105,13 +108,15 @@ int launch_batch(fse_ctx *ctx, Slot &s) {
         uint8_t *dl = static_cast<uint8_t *>(ws.d_luma.ptr) + r->io_off;
         uint8_t *dm = static_cast<uint8_t *>(ws.d_mask.ptr) + r->io_off;
         uint8_t *dout = static_cast<uint8_t *>(ws.d_out.ptr) + r->io_off;
-        const size_t bytes = (size_t)h.width * h.height;
-        if (cudaMemcpyAsync(dl, pl, bytes, cudaMemcpyHostToDevice, s.stream) != cudaSuccess ||
-            cudaMemcpyAsync(dm, pm, bytes, cudaMemcpyHostToDevice, s.stream) != cudaSuccess) {
+        const int dp = device_pitch(h);
+        if (cudaMemcpy2DAsync(dl, dp, pl, h.width, h.width, h.height, cudaMemcpyHostToDevice,
+                              s.stream) != cudaSuccess ||
+            cudaMemcpy2DAsync(dm, dp, pm, h.width, h.width, h.height, cudaMemcpyHostToDevice,
+                              s.stream) != cudaSuccess) {
             cudaGetLastError();
             return FSE_ECUDA;
         }
-        dev[i] = fse_frame{dl, dout, dm, h.width, h.height, h.width};
+        dev[i] = fse_frame{dl, dout, dm, h.width, h.height, dp};
         int cnt = 0;
         for (uint8_t v : lost[i]) cnt += v != 0;
         r->stats.lost_blocks = cnt;
@@ -122,8 +127,9 @@ int launch_batch(fse_ctx *ctx, Slot &s) {
     for (int i = 0; i < n; ++i) {
         Request *r = s.reqs[i];
         s.reqs[i]->stats.groups = ws.groups;  // max over the batch
-        if (cudaMemcpyAsync(io + r->io_off, dev[i].out, (size_t)r->frame.width * r->frame.height,
-                            cudaMemcpyDeviceToHost, s.stream) != cudaSuccess) {
+        if (cudaMemcpy2DAsync(io + r->io_off, r->frame.width, dev[i].out, dev[i].stride,
+                              r->frame.width, r->frame.height, cudaMemcpyDeviceToHost,
+                              s.stream) != cudaSuccess) {
             cudaGetLastError();
             return FSE_ECUDA;
         }
