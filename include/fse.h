@@ -129,6 +129,29 @@ int fse_plan_order(int bw, int bh, const uint8_t *block_lost, int order,
                    int32_t *group_of_block, int32_t *group_ptr,
                    int32_t *block_ids, int32_t *n_groups);
 
+/* Claim order of the lost blocks of n_frames frames for the executors (host
+ * only; no counterpart in the paper, which states the groups' order only).
+ * Lost block s depends on lost block d when d lies within the area footprint
+ * of s (+-16/B blocks) and has a smaller group: s reads d's concealed samples
+ * (class R, Sec. 2).  Every order with dependencies first gives the result of
+ * the group order (Sec. 3).
+ * Inputs: per frame bw[i], bh[i]; group_of_block = the frames' group maps
+ * (as from fse_plan_order) concatenated, frame i's [bh[i]*bw[i]] after
+ * frame i-1's; block = B (16, 8, 4 or 2).
+ * mode 0 (one launch per level): level = 1 + the largest level of the
+ *   block's dependencies, 0 without; items sorted by level, then frame, then
+ *   group order; level_start [lost blocks + 1] receives the first item of
+ *   each level and the total, n_levels the number of levels.
+ * mode 1 (persistent executor with `workers` CTAs claiming in order): list
+ *   schedule with unit block times, longest chain of dependants first; each
+ *   round starts up to `workers` ready blocks.  level_start / n_levels unused.
+ * Output, caller-owned: items [2 * lost blocks] (frame, block) pairs.
+ * Errors: FSE_EINVAL on NULL pointers, a dimension <= 0, an unsupported
+ * block size, an unknown mode or workers <= 0 in mode 1. */
+int fse_plan_claims(int n_frames, const int32_t *bw, const int32_t *bh,
+                    const int32_t *group_of_block, int block, int workers, int mode,
+                    int32_t *items, int32_t *level_start, int32_t *n_levels);
+
 /* Create a context on CUDA device `device`.  mem_budget bounds the device
  * workspace the context may hold (0 = no limit).  The context owns its
  * workspace (FP32 working frames, plans, status words) and a serving

@@ -22,7 +22,7 @@ FSE_EXEC_GROUPS, FSE_EXEC_PERSISTENT = 0, 1
 FSE_MAX_ITERS = 1024
 
 EXPORTED = [
-    "fse_plan_order", "fse_ctx_create", "fse_ctx_destroy", "fse_conceal_batch",
+    "fse_plan_order", "fse_plan_claims", "fse_ctx_create", "fse_ctx_destroy", "fse_conceal_batch",
     "fse_conceal_batch_host", "fse_extrapolate_areas", "fse_submit", "fse_poll",
     "fse_drain", "fse_last_batch_info", "fse_ctx_set_option", "fse_copy_work", "fse_copy_trace", "fse_last_kernel_ms", "fse_conceal_frame_noalloc", "fse_strerror",
 ]
@@ -70,6 +70,7 @@ def lib() -> ctypes.CDLL:
     L = ctypes.CDLL(LIB_PATH)
     vp, i32, cint = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int
     L.fse_plan_order.argtypes = [cint, cint, vp, cint, vp, vp, vp, ctypes.POINTER(i32)]
+    L.fse_plan_claims.argtypes = [cint, vp, vp, vp, cint, cint, cint, vp, vp, ctypes.POINTER(i32)]
     L.fse_ctx_create.argtypes = [ctypes.POINTER(vp), cint, ctypes.c_size_t]
     L.fse_ctx_destroy.argtypes = [vp]
     L.fse_ctx_destroy.restype = None
@@ -131,6 +132,25 @@ def fse_plan_order(block_lost: np.ndarray, order: int):
            "fse_plan_order")
     n = ng.value
     return gob.reshape(bh, bw), gptr[:n + 1].copy(), ids[:int(gptr[n])].copy()
+
+
+def fse_plan_claims(group_maps, block: int = 16, workers: int = 0, mode: int = 0):
+    """Claim order of the lost blocks of several frames (group maps as from
+    fse_plan_order).  Returns (items [L, 2] int32 (frame, block), level_start
+    [levels + 1] or None in mode 1)."""
+    maps = [np.ascontiguousarray(g, dtype=np.int32) for g in group_maps]
+    bw = np.array([g.shape[1] for g in maps], np.int32)
+    bh = np.array([g.shape[0] for g in maps], np.int32)
+    flat = np.concatenate([g.ravel() for g in maps]) if maps else np.zeros(0, np.int32)
+    lost = int((flat >= 0).sum())
+    items = np.zeros((max(lost, 1), 2), np.int32)
+    level_start = np.zeros(lost + 2, np.int32)
+    nl = ctypes.c_int32(0)
+    _check(lib().fse_plan_claims(len(maps), bw.ctypes.data, bh.ctypes.data, flat.ctypes.data,
+                                 int(block), int(workers), int(mode), items.ctypes.data,
+                                 level_start.ctypes.data, ctypes.byref(nl)),
+           "fse_plan_claims")
+    return items[:lost].copy(), (level_start[:nl.value + 1].copy() if mode == 0 else None)
 
 
 def _stream_handle(stream) -> int:

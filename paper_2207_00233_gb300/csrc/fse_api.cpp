@@ -1,6 +1,7 @@
 // Host runtime of the FSE library: context, device workspace, the batch
-// executors (one launch per processing-order group, or one persistent
-// launch over a dependency graph), and the inspection entry point.
+// executors (one launch per dependency level, or one persistent launch whose
+// CTAs claim blocks in a list-schedule order and wait on completion flags),
+// and the inspection entry point.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -373,9 +374,12 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
     }
 
     // ---- processing order per frame (host, integer; frames in parallel) ----
+    // and the dependency depths of each frame's lost blocks
     std::vector<int32_t> gob_h(nblocks);
     std::vector<std::vector<int32_t>> frame_gptr(n), frame_ids(n);
+    std::vector<FrameDepths> depths(n);
     std::vector<int> plan_rc(n, FSE_OK);
+    const int rad = kBorder >> block_log2(p->block);
     auto plan_one = [&](int i) {
         const int nb = fd[i].bh * fd[i].bw;
         std::vector<int32_t> gptr(nb + 1, 0), ids(nb, 0);
@@ -385,6 +389,13 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
         if (plan_rc[i]) return;
         frame_gptr[i].assign(gptr.begin(), gptr.begin() + ng + 1);
         frame_ids[i].assign(ids.begin(), ids.begin() + gptr[ng]);
+        FrameDepths &f = depths[i];
+        f.bw = fd[i].bw;
+        f.bh = fd[i].bh;
+        f.gob = gob_h.data() + lost_off[i];
+        f.ids = frame_ids[i].data();
+        f.n = (int)frame_ids[i].size();
+        frame_depths(f, rad);
     };
     {
         const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
@@ -409,21 +420,22 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
         lost_blocks += frame_gptr[i][ng];
     }
 
-    // ---- work items ----
-    std::vector<int2> items;
-    items.reserve(lost_blocks);
-    std::vector<int> group_start(max_groups + 1, 0);
-    for (int g = 0; g < max_groups; ++g) {
-        group_start[g] = (int)items.size();
-        for (int i = 0; i < n; ++i) {
-            const auto &gp = frame_gptr[i];
-            if (g + 1 >= (int)gp.size()) continue;
-            for (int j = gp[g]; j < gp[g + 1]; ++j) items.push_back(make_int2(i, frame_ids[i][j]));
-        }
-    }
-    group_start[max_groups] = (int)items.size();
-
+    // ---- work items: one launch per dependency level, or the claim order
+    // of the persistent CTAs ----
     const bool persistent = p->executor == FSE_EXEC_PERSISTENT;
+    int grid = 0;
+    if (persistent) {
+        int per_sm = max_resident_ctas(p->iters);
+        if (ctx->persistent_ctas > 0) per_sm = std::min(per_sm, ctx->persistent_ctas);
+        grid = std::min<int>(lost_blocks, ctx->num_sms * per_sm);
+    }
+    std::vector<int2> items;
+    std::vector<int> level_start;
+    if (persistent)
+        schedule_claims(depths, rad, std::max(grid, 1), items);
+    else
+        level_claims(depths, items, level_start);
+    const int n_launch_levels = persistent ? 0 : (int)level_start.size() - 1;
 
     // ---- uploads ----
     const size_t n_items = items.size();
@@ -506,16 +518,13 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
             wq.n = (int)n_items;
             wq.stuck_item = stuck_item;
             wq.spin_limit = ctx->spin_limit;
-            int per_sm = max_resident_ctas(p->iters);
-            if (ctx->persistent_ctas > 0) per_sm = std::min(per_sm, ctx->persistent_ctas);
-            const int grid = std::min<int>((int)n_items, ctx->num_sms * per_sm);
             CK(launch_persistent(fdev, wq, kp, rho_tab, tw_tab, p->precision, grid, stream));
             launches += 1;
         } else {
             const int2 *idev = static_cast<const int2 *>(ws.items.ptr);
-            for (int g = 0; g < max_groups; ++g) {
-                const int cnt = group_start[g + 1] - group_start[g];
-                CK(launch_group(fdev, idev + group_start[g], cnt, kp, rho_tab, tw_tab,
+            for (int l = 0; l < n_launch_levels; ++l) {
+                const int cnt = level_start[l + 1] - level_start[l];
+                CK(launch_group(fdev, idev + level_start[l], cnt, kp, rho_tab, tw_tab,
                                 p->precision, stream));
                 launches += 1;
             }

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -121,10 +122,10 @@ struct FrameDesc {
                              // aligned, or null: gather with plain loads
 };
 
-// Work of the persistent executor: items are (frame, block) pairs in group
-// order.  A claimed item waits until every earlier-group lost block whose
-// samples lie in its area has set its completion flag; claims follow the
-// group order, so every awaited block was claimed earlier by a running CTA.
+// Work of the persistent executor: items are (frame, block) pairs in a claim
+// order in which every block follows its dependencies (the earlier-group lost
+// blocks within its area footprint).  A claimed item waits until those have
+// set their completion flags; each was claimed earlier by a running CTA.
 struct WorkQueue {
     const int2 *items;       // [n] (frame, block)
     int *head;               // work counter
@@ -155,6 +156,27 @@ cudaError_t launch_areas(const float *area_f, const uint8_t *area_cls, int n,
                          int32_t *u_out, float *dc_out, float *r_out,
                          cudaStream_t stream);
 int max_resident_ctas(int iters);   // CTAs of the block kernel per SM
+
+// Claim order of a batch (host, fse_sched.cpp).  Per frame: the block grid,
+// the group of each block and the lost blocks in group order; frame_depths
+// fills, per block, the dependency level, the height (longest chain of
+// dependants, counting the block) and the number of dependencies, for the
+// footprint radius rad = 16 / B blocks.
+struct FrameDepths {
+    int bw = 0, bh = 0;
+    const int32_t *gob = nullptr;
+    const int32_t *ids = nullptr;
+    int n = 0;
+    std::vector<int32_t> own_ids;               // storage of ids, when owned
+    std::vector<int32_t> level, height, indeg, pos;
+};
+void frame_depths(FrameDepths &f, int rad);
+// Items by level (independent sets); level_start[l] .. level_start[l + 1].
+void level_claims(const std::vector<FrameDepths> &frames, std::vector<int2> &items,
+                  std::vector<int> &level_start);
+// Items in list-schedule order for `workers` CTAs (consumes indeg).
+void schedule_claims(std::vector<FrameDepths> &frames, int rad, int workers,
+                     std::vector<int2> &items);
 bool precision_supported(int precision);
 
 }  // namespace fse

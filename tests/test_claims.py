@@ -1,0 +1,138 @@
+"""Claim order of the executors (host logic, no GPU): one launch per
+dependency level, or the list schedule of the persistent CTAs.  A lost block
+depends on the earlier-group lost blocks within its area footprint
+(+-16/B blocks), whose concealed samples it reads as class R (Sec. 2, 3)."""
+import heapq
+
+import numpy as np
+import pytest
+
+import fse_synth
+
+fse = pytest.importorskip("paper_2207_00233_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2207_00233_gb300 import build
+    build.build()
+
+
+def _deps(gob, rad):
+    bh, bw = gob.shape
+    out = {}
+    for by, bx in np.argwhere(gob >= 0):
+        g = gob[by, bx]
+        d = []
+        for y in range(max(0, by - rad), min(bh, by + rad + 1)):
+            for x in range(max(0, bx - rad), min(bw, bx + rad + 1)):
+                if 0 <= gob[y, x] < g:
+                    d.append(y * bw + x)
+        out[by * bw + bx] = d
+    return out
+
+
+def _frames(seed, n=3, bh=9, bw=13, B=16):
+    rng = np.random.default_rng(seed)
+    maps = []
+    for i in range(n):
+        lost = fse_synth.mixed_block_mask(bh, bw, 0.3 + 0.1 * i, rng).astype(np.uint8)
+        gob, _, _ = fse.fse_plan_order(lost, fse.FSE_ORDER_OPTIMIZED)
+        maps.append(gob)
+    return maps
+
+
+@pytest.mark.parametrize("B", [16, 8, 4, 2])
+def test_levels_are_independent_sets_in_dependency_order(B):
+    rad = 16 // B
+    maps = _frames(10 + B)
+    items, ls = fse.fse_plan_claims(maps, block=B, mode=0)
+    deps = [_deps(g, rad) for g in maps]
+    # a permutation of the lost blocks
+    want = sorted((f, b) for f, g in enumerate(maps) for b in np.flatnonzero(g.ravel() >= 0))
+    assert sorted(map(tuple, items.tolist())) == want
+    assert ls[0] == 0 and ls[-1] == len(items)
+    level = {}
+    for l in range(len(ls) - 1):
+        for f, b in items[ls[l]:ls[l + 1]]:
+            level[(f, b)] = l
+    for (f, b), l in level.items():
+        # exactly 1 + the deepest dependency: dependencies come in earlier
+        # launches and nothing in the same launch depends on another
+        assert l == 1 + max((level[(f, d)] for d in deps[f][b]), default=-1)
+
+
+def _list_schedule(maps, rad, P):
+    """Rounds of P starts, ready blocks by (longest chain of dependants,
+    frame, group order), dependants ready in the next round."""
+    deps = [_deps(g, rad) for g in maps]
+    succ, indeg, height, pos = {}, {}, {}, {}
+    for f, g in enumerate(maps):
+        order = sorted(deps[f], key=lambda b: (g.ravel()[b], b))
+        for j, b in enumerate(order):
+            pos[(f, b)] = j
+            indeg[(f, b)] = len(deps[f][b])
+            for d in deps[f][b]:
+                succ.setdefault((f, d), []).append((f, b))
+        for b in reversed(order):
+            height[(f, b)] = 1 + max((height[s] for s in succ.get((f, b), [])), default=0)
+    ready = [(-height[k], k[0], pos[k], k) for k in indeg if indeg[k] == 0]
+    heapq.heapify(ready)
+    out = []
+    while ready:
+        rel = []
+        for _ in range(min(P, len(ready))):
+            *_, k = heapq.heappop(ready)
+            out.append(k)
+            for s in succ.get(k, []):
+                indeg[s] -= 1
+                if indeg[s] == 0:
+                    rel.append(s)
+        for s in rel:
+            heapq.heappush(ready, (-height[s], s[0], pos[s], s))
+    return out
+
+
+@pytest.mark.parametrize("B,P", [(16, 5), (16, 64), (8, 7), (2, 16)])
+def test_schedule_matches_list_scheduling(B, P):
+    maps = _frames(20 + B, n=2, bh=7, bw=11)
+    items, ls = fse.fse_plan_claims(maps, block=B, workers=P, mode=1)
+    assert ls is None
+    assert [tuple(t) for t in items.tolist()] == _list_schedule(maps, 16 // B, P)
+
+
+def test_schedule_is_topological_on_a_full_hd_frame():
+    img, mask = fse_synth.workload_batch_1080p(1)[0]
+    bh, bw = (img.shape[0] + 15) // 16, (img.shape[1] + 15) // 16
+    pm = np.zeros((bh * 16, bw * 16), np.uint8)
+    pm[:img.shape[0], :img.shape[1]] = mask
+    lost = (pm.reshape(bh, 16, bw, 16).max(axis=(1, 3)) > 0).astype(np.uint8)
+    gob, _, _ = fse.fse_plan_order(lost, fse.FSE_ORDER_OPTIMIZED)
+    items, _ = fse.fse_plan_claims([gob], block=16, workers=456, mode=1)
+    seen = np.zeros(bh * bw, bool)
+    deps = _deps(gob, 1)
+    for _, b in items:
+        assert all(seen[d] for d in deps[b])
+        seen[b] = True
+    assert seen.sum() == (gob >= 0).sum()
+
+
+def test_single_level_without_dependencies():
+    gob = np.full((4, 5), -1, np.int32)
+    gob[0, 0] = 0
+    gob[3, 4] = 2  # far apart: independent
+    items, ls = fse.fse_plan_claims([gob], mode=0)
+    assert ls.tolist() == [0, 2] and sorted(items[:, 1].tolist()) == [0, 19]
+    none = np.full((2, 2), -1, np.int32)
+    items, ls = fse.fse_plan_claims([none], mode=0)
+    assert len(items) == 0 and ls.tolist() == [0]
+
+
+def test_invalid_arguments():
+    gob = np.zeros((2, 2), np.int32)
+    with pytest.raises(fse.FseError):
+        fse.fse_plan_claims([gob], block=3)
+    with pytest.raises(fse.FseError):
+        fse.fse_plan_claims([gob], mode=2)
+    with pytest.raises(fse.FseError):
+        fse.fse_plan_claims([gob], mode=1, workers=0)
