@@ -31,7 +31,9 @@ constexpr int kW4Bytes = kW4Rows * kDft * 16;          // 72704
 constexpr int kTwOff = kW4Bytes;                       // 64 x float2
 constexpr int kRedOff = kTwOff + kDft * 8;             // reduction scratch
 constexpr int kRedBytes = 8 * 4 + 8 * 16 + 64;         // smax[8], cand[8], misc
-constexpr int kListOff = kRedOff + kRedBytes;          // dc list, then u list
+constexpr int kXrwOff = kRedOff + kRedBytes;           // W's real columns (FP32 projection)
+constexpr int kXrwBytes = 2 * 33 * 8;                  // columns k_n = 0, 32; rows 0..32
+constexpr int kListOff = kXrwOff + kXrwBytes;          // dc list, then u list
 // misc[2..3]: TMA mbarrier, misc[4]: its next phase parity, misc[5..6]: the
 // persistent executor's claimed item and wait result
 constexpr int kMbarOff = kRedOff + 8 * 4 + 8 * 16 + 8;
@@ -50,6 +52,11 @@ constexpr int kHalfCols = kDft / 2 + 1;                         // 33 (real inpu
 constexpr int kYxOff = kWTileOff + kArea * kTileStride * 4;     // 48x33 float2
 constexpr int kYwOff = kYxOff + kArea * kHalfCols * 8;          // 48x33 float2
 static_assert(kYwOff + kArea * kHalfCols * 8 <= kW4Bytes, "scratch overflow");
+// Column-DFT intermediates of the FP32 projection (33 x 132 floats each):
+// the x input's in the (then free) tile region, the w input's after the
+// half spectra.
+constexpr int kTswOff = kYwOff + kArea * kHalfCols * 8;         // 44160
+static_assert(kTswOff + 33 * 132 * 4 <= kW4Bytes, "column-DFT scratch overflow");
 // After the iterations the W4 region holds the synthesis tables, in chunks
 // of kSynChunk iterations: P[it][i] = dc_it exp(+j 2 pi u_m (16+i) / 64) and
 // E[it][j] = exp(+j 2 pi u_n (16+j) / 64), 16 complex values each.

@@ -244,29 +244,135 @@ struct Trace {
 // Stage 2 of the projection for the entries of thread (w, l):
 // X[k_m][k_n] = sum_m exp(-j 2 pi k_m m / 64) Y[m][k_n] for k_m = 8w + r and
 // k_n in {l, l + 32}; column l + 32 comes from the conjugate of 32 - l.
-__device__ __forceinline__ void stage2_rows(const float2 *y, const float2 *tw, int w, int l,
-                                            float (&ar)[8][2], float (&ai)[8][2]) {
-    for (int m = 0; m < kArea; ++m) {
-        const float2 a = y[m * kHalfCols + l];
-        float2 b = y[m * kHalfCols + 32 - l];
-        b.y = -b.y;
-        const int t0 = (8 * w * m) & (kDft - 1);
+// Lane 0 of each warp: entries of the real columns k_n = 0 and 32 for the
+// warp's rows k_m = 8w + r, from xr (conjugated for k_m > 32).
+__device__ __forceinline__ void real_cols(const float2 *xr, int w, int r, float &re0,
+                                          float &im0, float &re1, float &im1) {
+    const int k = 8 * w + r;
+    const bool lo = k <= kDft / 2;
+    const int kk = lo ? k : kDft - k;
+    // loaded where used (the memory clobber keeps the compiler from hoisting
+    // all sixteen loads, which would cost registers)
+    float ar, ai, br, bi;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
+                 : "=f"(ar), "=f"(ai) : "r"(smem_addr(xr + kk)) : "memory");
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
+                 : "=f"(br), "=f"(bi) : "r"(smem_addr(xr + kHalfCols + kk)) : "memory");
+    re0 = ar;
+    im0 = lo ? ai : -ai;
+    re1 = br;
+    im1 = lo ? bi : -bi;
+}
+
+// Column DFT of the half spectrum y[48][33] (rows m, columns k_n) of one
+// input, split as m = 8a + b (a < 6) and k_m = r + 8 q:
+//   X[r + 8q][k_n] = sum_b e^{-j 2 pi b q / 8} T[b][r],
+//   T[b][r] = e^{-j 2 pi r b / 64} sum_a y[8a + b][k_n] e^{-j 2 pi r a / 8}
+// (the 64-point DFT as 8-point DFTs with twiddles; about a quarter of the
+// multiply-adds of the direct sums, and shorter sums).
+//
+// Step 1: thread (w, l) computes T for b = w and column k_n = l and stores it
+// as ts[k_n][8b + r] (complex; row stride kTsStride floats, so that the
+// 16-byte loads of eight consecutive lanes fall into distinct banks).
+//
+// Columns k_n = 0 and 32 of a real input's spectrum are themselves
+// conjugate-symmetric in k_m, so |R_w| ties exactly between k_m and -k_m
+// there (as everywhere between k and -k before the first update).  The
+// selection resolves exact ties to the smallest index, so the FP32 spectrum
+// must keep the symmetry bit for bit: those two columns are summed directly
+// for k_m <= 32 (xr[c][k_m]) and conjugated for k_m > 32.  Elsewhere the
+// mirrored column repeats the partner entry's arithmetic exactly.
+constexpr int kTsStride = 132;
+constexpr int kXrOff = kHalfCols * kTsStride * 4;  // after ts of the x input
+static_assert(kXrOff % 16 == 0 && kXrOff + 2 * 2 * kHalfCols * 8 <=
+                                       kXTileOff + 2 * kArea * kTileStride * 4,
+              "column-DFT scratch must fit the area tiles");
+__device__ __forceinline__ void col_dft_step1(const float2 *y, float *ts, const float2 *tw,
+                                              int b, int c) {
+    float2 v[6];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const float2 cs = tw[(t0 + r * m) & (kDft - 1)];
-            // (c - j s) (y_r + j y_i) = (c y_r + s y_i) + j (c y_i - s y_r)
-            ar[r][0] = fmaf(cs.x, a.x, fmaf(cs.y, a.y, ar[r][0]));
-            ai[r][0] = fmaf(cs.x, a.y, fmaf(-cs.y, a.x, ai[r][0]));
-            ar[r][1] = fmaf(cs.x, b.x, fmaf(cs.y, b.y, ar[r][1]));
-            ai[r][1] = fmaf(cs.x, b.y, fmaf(-cs.y, b.x, ai[r][1]));
+    for (int a = 0; a < 6; ++a) v[a] = y[(8 * a + b) * kHalfCols + c];
+    float4 *out = reinterpret_cast<float4 *>(ts + c * kTsStride + 16 * b);
+#pragma unroll
+    for (int r = 0; r < 8; r += 2) {
+        float t[4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float zr = 0.f, zi = 0.f;
+#pragma unroll
+            for (int a = 0; a < 6; ++a) {
+                // (c - j s) (v_r + j v_i)
+                const float2 cs = tw[(8 * (r + h) * a) & (kDft - 1)];
+                zr = fmaf(cs.x, v[a].x, fmaf(cs.y, v[a].y, zr));
+                zi = fmaf(cs.x, v[a].y, fmaf(-cs.y, v[a].x, zi));
+            }
+            const float2 cs = tw[((r + h) * b) & (kDft - 1)];
+            t[2 * h] = fmaf(cs.x, zr, cs.y * zi);
+            t[2 * h + 1] = fmaf(cs.x, zi, -cs.y * zr);
         }
+        out[r / 2] = make_float4(t[0], t[1], t[2], t[3]);
     }
 }
 
-// ---- projection on the FP32 pipes --------------------------------------------
-// Stage 1 (along n) for both inputs, using the conjugate symmetry of a real
-// input's spectrum: Y[m][k_n] for k_n = 0..32.  Stage 2 (along m) produces
-// the entries each thread owns: R_w into registers, W into temporaries.
+// Step 2: thread (w, l) sums its rows k_m = 8w + r (q = w) of column l, and
+// of column l + 32 through the conjugate symmetry of a real input's
+// spectrum: X[k_m][l + 32] = conj(X[-k_m][32 - l]), where -k_m = r' + 8 q'
+// with r' = -r mod 8 and q' = (8 - w) mod 8 for r = 0, 7 - w otherwise.
+// Columns 0 and 32, rows 0..32: xr[c][k] (c = 0: k_n = 0, c = 1: k_n = 32)
+// for the real column y[.][k_n] (its imaginary parts are exactly zero).
+__device__ __forceinline__ void col_dft_real(const float2 *y, float2 *xr, const float2 *tw,
+                                             int e) {
+    const int c = e / kHalfCols, k = e - c * kHalfCols;
+    const float2 *col = y + (c ? kHalfCols - 1 : 0);
+    float re = 0.f, im = 0.f;
+    for (int m = 0; m < kArea; ++m) {
+        const float v = col[m * kHalfCols].x;
+        const float2 cs = tw[(k * m) & (kDft - 1)];
+        re = fmaf(v, cs.x, re);
+        im = fmaf(-v, cs.y, im);
+    }
+    xr[e] = make_float2(re, im);
+}
+
+__device__ __forceinline__ void col_dft_step2(const float *ts, const float2 *tw, int w, int l,
+                                              float (&ar)[8][2], float (&ai)[8][2]) {
+    const float4 *dl = reinterpret_cast<const float4 *>(ts + l * kTsStride);
+    const float4 *cl = reinterpret_cast<const float4 *>(ts + (32 - l) * kTsStride);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) ar[r][0] = ai[r][0] = ar[r][1] = ai[r][1] = 0.f;
+#pragma unroll 1
+    for (int b = 0; b < 8; ++b) {
+        const float2 cq = tw[(8 * w * b) & (kDft - 1)];        // e^{-j 2 pi b w / 8}
+        const float2 cq7 = tw[(8 * (7 - w) * b) & (kDft - 1)];  // e^{-j 2 pi b (7 - w) / 8}
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            // direct column: (c - j s) T[b][r], r = 2k, 2k + 1
+            const float4 x = dl[4 * b + k];
+            ar[2 * k][0] = fmaf(cq.x, x.x, fmaf(cq.y, x.y, ar[2 * k][0]));
+            ai[2 * k][0] = fmaf(cq.x, x.y, fmaf(-cq.y, x.x, ai[2 * k][0]));
+            ar[2 * k + 1][0] = fmaf(cq.x, x.z, fmaf(cq.y, x.w, ar[2 * k + 1][0]));
+            ai[2 * k + 1][0] = fmaf(cq.x, x.w, fmaf(-cq.y, x.z, ai[2 * k + 1][0]));
+            // mirrored column (conjugated at the end): T[b][r'] serves the
+            // row r = -r' mod 8
+            const float4 y = cl[4 * b + k];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int rp = 2 * k + h, r = (8 - rp) & 7;
+                const float tr = h ? y.z : y.x, ti = h ? y.w : y.y;
+                if (r == 0) {  // e^{+j 2 pi b w / 8} = (c + j s)
+                    ar[r][1] = fmaf(cq.x, tr, fmaf(-cq.y, ti, ar[r][1]));
+                    ai[r][1] = fmaf(cq.x, ti, fmaf(cq.y, tr, ai[r][1]));
+                } else {
+                    ar[r][1] = fmaf(cq7.x, tr, fmaf(cq7.y, ti, ar[r][1]));
+                    ai[r][1] = fmaf(cq7.x, ti, fmaf(-cq7.y, tr, ai[r][1]));
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) ai[r][1] = -ai[r][1];
+}
+
 __device__ __forceinline__ void project_fp32(unsigned char *smem, const float2 *tw,
                                              u64 (&rre)[8], u64 (&rim)[8],
                                              float (&wre)[8][2], float (&wim)[8][2]) {
@@ -310,21 +416,40 @@ __device__ __forceinline__ void project_fp32(unsigned char *smem, const float2 *
     __syncthreads();
 
     const int w = tid >> 5, l = tid & 31;
-    // x pass, then w pass: only one set of accumulators grows at a time.
+    // Column DFTs: step 1 for both inputs (x into the free tile region, w
+    // behind the half spectra), then step 2, x first.
+    float *tsx = reinterpret_cast<float *>(smem + kXTileOff);
+    float *tsw = reinterpret_cast<float *>(smem + kTswOff);
+    float2 *xrx = reinterpret_cast<float2 *>(smem + kXrOff);
+    col_dft_step1(yx, tsx, tw, w, l);
+    col_dft_step1(yw, tsw, tw, w, l);
+    if (tid < 2 * kHalfCols) {
+        col_dft_real(yx, xrx, tw, tid);
+        col_dft_real(yw, reinterpret_cast<float2 *>(smem + kXrwOff), tw, tid);
+    }
+    __syncthreads();
     {
         float ar[8][2], ai[8][2];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) ar[r][0] = ar[r][1] = ai[r][0] = ai[r][1] = 0.f;
-        stage2_rows(yx, tw, w, l, ar, ai);
+        col_dft_step2(tsx, tw, w, l, ar, ai);
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             rre[r] = pack2(ar[r][0], ar[r][1]);
             rim[r] = pack2(ai[r][0], ai[r][1]);
         }
     }
+    if (l == 0) {
 #pragma unroll
-    for (int r = 0; r < 8; ++r) wre[r][0] = wre[r][1] = wim[r][0] = wim[r][1] = 0.f;
-    stage2_rows(yw, tw, w, l, wre, wim);
+        for (int r = 0; r < 8; ++r) {
+            float a, b, c, d;
+            real_cols(xrx, w, r, a, b, c, d);
+            rre[r] = pack2(a, c);
+            rim[r] = pack2(b, d);
+        }
+    }
+    // W's real columns are taken from xr when W is stored (store_w4): after
+    // a selection of a self-conjugate index (the DC term, say) the residual
+    // stays conjugate-symmetric only if W is.
+    col_dft_step2(tsw, tw, w, l, wre, wim);
 }
 
 // ---- projection on the tensor cores (warp-level mma.sync) --------------------
@@ -639,8 +764,10 @@ __device__ __forceinline__ void store_w4_frags(unsigned char *smem, const float 
 }
 
 // Store the thread's W entries in the W4 layout (plus the repeated rows).
+// Lane 0 then rewrites the real columns k_n = 0 and 32 from xr (exactly
+// conjugate-symmetric in k_m; see col_dft_step1).
 __device__ __forceinline__ void store_w4(unsigned char *smem, const float (&wre)[8][2],
-                                         const float (&wim)[8][2]) {
+                                         const float (&wim)[8][2], const float2 *xr) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     float4 *w4 = reinterpret_cast<float4 *>(smem);
 #pragma unroll
@@ -653,6 +780,19 @@ __device__ __forceinline__ void store_w4(unsigned char *smem, const float (&wre)
         if (row < kW4Rows - kDft) {
             w4[(row + kDft) * kDft + l] = a;
             w4[(row + kDft) * kDft + l + 32] = b;
+        }
+    }
+    if (l != 0) return;
+    for (int r = 0; r < 8; ++r) {
+        const int row = 8 * w + r;
+        float4 a;
+        real_cols(xr, w, r, a.x, a.z, a.y, a.w);
+        const float4 b = make_float4(a.y, a.x, a.w, a.z);
+        w4[row * kDft] = a;
+        w4[row * kDft + 32] = b;
+        if (row < kW4Rows - kDft) {
+            w4[(row + kDft) * kDft] = a;
+            w4[(row + kDft) * kDft + 32] = b;
         }
     }
 }
@@ -709,8 +849,9 @@ __device__ __forceinline__ float run_block(const Src &src, const KParams &kp,
         float wre[8][2], wim[8][2];
         project_fp32(smem, tw, rre, rim, wre, wim);
         __syncthreads();  // all reads of the stage-1 scratch are done
-        store_w4(smem, wre, wim);
-        if (tid == 0) misc[0] = wre[0][0];  // W[0] = sum of the weights
+        const float2 *xrw = reinterpret_cast<const float2 *>(smem + kXrwOff);
+        store_w4(smem, wre, wim, xrw);
+        if (tid == 0) misc[0] = xrw[0].x;  // W[0] = sum of the weights
     } else {
         float wacc[5][4];
         project_mma<P>(smem, kp.frags, rre, rim, wacc);
