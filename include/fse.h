@@ -142,9 +142,15 @@ int fse_plan_order(int bw, int bh, const uint8_t *block_lost, int order,
  *   block's dependencies, 0 without; items sorted by level, then frame, then
  *   group order; level_start [lost blocks + 1] receives the first item of
  *   each level and the total, n_levels the number of levels.
- * mode 1 (persistent executor with `workers` CTAs claiming in order): list
- *   schedule with unit block times, longest chain of dependants first; each
- *   round starts up to `workers` ready blocks.  level_start / n_levels unused.
+ * mode 1 (for comparison): list schedule of `workers` CTAs with unit block
+ *   times, longest chain of dependants first (ties: ready first; initially
+ *   frame by frame in group order, later in order of release); each round
+ *   starts up to `workers` ready blocks, whose dependants become ready in
+ *   the next round.
+ * mode 2 (persistent executor): longest chain of dependants first (height,
+ *   counting the block), then frame, then group order; topological because
+ *   a block's height exceeds its dependants'.
+ * level_start / n_levels are used in mode 0 only.
  * Output, caller-owned: items [2 * lost blocks] (frame, block) pairs.
  * Errors: FSE_EINVAL on NULL pointers, a dimension <= 0, an unsupported
  * block size, an unknown mode or workers <= 0 in mode 1. */

@@ -272,6 +272,69 @@ static int check_frame(const fse_frame &f) {
         }                                          \
     } while (0)
 
+// ---------------------------------------------------------------------------
+// Host worker pool
+// ---------------------------------------------------------------------------
+
+fse::WorkerPool::~WorkerPool() {
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto &t : threads_) t.join();
+}
+
+void fse::WorkerPool::worker() {
+    unsigned seen = 0;
+    std::unique_lock<std::mutex> lk(mu_);
+    for (;;) {
+        cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+        if (stop_) return;
+        seen = gen_;
+        const std::function<void(int)> *fn = fn_;
+        const int n = n_;
+        lk.unlock();
+        for (int i = next_.fetch_add(1); i < n; i = next_.fetch_add(1)) (*fn)(i);
+        lk.lock();
+        if (--active_ == 0) done_cv_.notify_one();
+    }
+}
+
+void fse::WorkerPool::run(int n, const std::function<void(int)> &fn) {
+    std::unique_lock<std::mutex> run_lk(run_mu_, std::try_to_lock);
+    if (n <= 1 || !run_lk.owns_lock()) {
+        for (int i = 0; i < n; ++i) fn(i);
+        return;
+    }
+    if (!started_) {
+        started_ = true;
+        const int hw = (int)std::thread::hardware_concurrency();
+        const int nt = std::min(std::max(hw - 1, 0), 15);
+        try {
+            for (int t = 0; t < nt; ++t) threads_.emplace_back([this] { worker(); });
+        } catch (...) {  // no threads: the calling thread does the work
+        }
+    }
+    if (threads_.empty()) {
+        for (int i = 0; i < n; ++i) fn(i);
+        return;
+    }
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        fn_ = &fn;
+        n_ = n;
+        next_.store(0);
+        active_ = (int)threads_.size();
+        ++gen_;
+    }
+    cv_.notify_all();
+    for (int i = next_.fetch_add(1); i < n; i = next_.fetch_add(1)) fn(i);
+    std::unique_lock<std::mutex> lk(mu_);
+    done_cv_.wait(lk, [&] { return active_ == 0; });
+    fn_ = nullptr;
+}
+
 int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
                    const fse_params *p, cudaStream_t stream,
                    const std::vector<std::vector<uint8_t>> *host_lost) {
@@ -397,21 +460,7 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
         f.n = (int)frame_ids[i].size();
         frame_depths(f, rad);
     };
-    {
-        const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
-        const int nt = std::min(n, hw);
-        if (nt <= 1) {
-            for (int i = 0; i < n; ++i) plan_one(i);
-        } else {
-            std::atomic<int> next{0};
-            std::vector<std::thread> pool;
-            for (int t = 0; t < nt; ++t)
-                pool.emplace_back([&] {
-                    for (int i = next++; i < n; i = next++) plan_one(i);
-                });
-            for (auto &th : pool) th.join();
-        }
-    }
+    ctx->pool.run(n, plan_one);
     int max_groups = 0, lost_blocks = 0;
     for (int i = 0; i < n; ++i) {
         if (plan_rc[i]) return plan_rc[i];
@@ -432,7 +481,7 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
     std::vector<int2> items;
     std::vector<int> level_start;
     if (persistent)
-        schedule_claims(depths, rad, std::max(grid, 1), items);
+        height_claims(depths, items);
     else
         level_claims(depths, items, level_start);
     const int n_launch_levels = persistent ? 0 : (int)level_start.size() - 1;

@@ -1,8 +1,10 @@
 // Context, workspace and serving state of the FSE library (host side).
 #pragma once
 
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <functional>
 #include <cstdint>
 #include <deque>
 #include <mutex>
@@ -65,6 +67,33 @@ struct Slot {
 
 int check_params(const fse_params *p);
 
+// Host worker threads of a context, started on first use and kept until the
+// context is destroyed (planning the frames of a batch in parallel without
+// starting threads on every call).
+class WorkerPool {
+public:
+    WorkerPool() = default;
+    WorkerPool(const WorkerPool &) = delete;
+    WorkerPool &operator=(const WorkerPool &) = delete;
+    ~WorkerPool();
+    // fn(i) for i in [0, n) on the workers and the calling thread; returns
+    // when all are done.  A call that finds the pool busy (another thread's
+    // batch) runs its jobs on the calling thread.
+    void run(int n, const std::function<void(int)> &fn);
+
+private:
+    void worker();
+    std::vector<std::thread> threads_;
+    std::mutex run_mu_;  // one run at a time
+    std::mutex mu_;      // guards the job description below
+    std::condition_variable cv_, done_cv_;
+    const std::function<void(int)> *fn_ = nullptr;
+    int n_ = 0, active_ = 0;
+    unsigned gen_ = 0;
+    bool stop_ = false, started_ = false;
+    std::atomic<int> next_{0};
+};
+
 }  // namespace fse
 
 struct fse_ctx {
@@ -81,6 +110,7 @@ struct fse_ctx {
     std::vector<std::pair<float, fse::DevBuf>> rho_tabs;  // Eq. (2) decay per (rho, block)
     fse::DevBuf frags[6];                                 // per precision (tensor cores)
     fse::Workspace ws;  // synchronous API
+    fse::WorkerPool pool;  // host planning threads
     std::mutex api_mu;  // one synchronous API call at a time
     std::mutex mem_mu;  // budget accounting and table cache
 

@@ -168,22 +168,29 @@ int max_resident_ctas(int iters);   // CTAs of the block kernel per SM
 // the group of each block and the lost blocks in group order; frame_depths
 // fills, per block, the dependency level, the height (longest chain of
 // dependants, counting the block) and the number of dependencies, for the
-// footprint radius rad = 16 / B blocks.
+// footprint radius rad = 16 / B blocks.  The per-block arrays live in a grid
+// padded by rad blocks of group -1 (no bounds tests in the footprint scans).
 struct FrameDepths {
     int bw = 0, bh = 0;
     const int32_t *gob = nullptr;
     const int32_t *ids = nullptr;
     int n = 0;
     std::vector<int32_t> own_ids;               // storage of ids, when owned
-    std::vector<int32_t> level, height, indeg, pos;
+    int rad = 0, pw = 0;                        // padding, padded row length
+    std::vector<int32_t> gp;                    // padded group map
+    std::vector<int32_t> nbr;                   // footprint offsets (no centre)
+    std::vector<int32_t> pid;                   // padded cell of ids[j]
+    std::vector<int32_t> level, height, indeg;  // per padded cell
+    int block_of(int c) const { return (c / pw - rad) * bw + (c % pw - rad); }
 };
 void frame_depths(FrameDepths &f, int rad);
 // Items by level (independent sets); level_start[l] .. level_start[l + 1].
 void level_claims(const std::vector<FrameDepths> &frames, std::vector<int2> &items,
                   std::vector<int> &level_start);
+// Items by height, descending (persistent executor).
+void height_claims(const std::vector<FrameDepths> &frames, std::vector<int2> &items);
 // Items in list-schedule order for `workers` CTAs (consumes indeg).
-void schedule_claims(std::vector<FrameDepths> &frames, int rad, int workers,
-                     std::vector<int2> &items);
+void schedule_claims(std::vector<FrameDepths> &frames, int workers, std::vector<int2> &items);
 bool precision_supported(int precision);
 
 }  // namespace fse

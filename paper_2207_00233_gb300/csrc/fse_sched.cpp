@@ -10,18 +10,22 @@
 // * Level order, for one launch per level: level(s) = 1 + the largest level
 //   of its dependencies (0 without); blocks of one level are independent.
 //   Levels are far fewer than groups (many groups do not touch each other).
-// * Schedule, for the persistent executor (P resident CTAs claim blocks in
-//   order and wait for the dependencies of what they claimed): list
-//   scheduling with unit block times, longest chain of dependants first.
-//   Each round starts the P ready blocks whose chains to the end are
-//   longest; dependants become ready in the next round.  Claims in that
-//   order rarely wait, and long chains start early enough not to form a
-//   tail.
+// * Height order, for the persistent executor (P resident CTAs claim blocks
+//   in order and wait for the dependencies of what they claimed): longest
+//   chain of dependants first (the height of a block exceeds that of every
+//   dependant, so the order is topological).  Long chains start early and
+//   do not form a tail; a claim rarely waits.  Static: a counting sort.
+// * Schedule (for comparison): list scheduling of P workers with unit
+//   block times, longest chain first among the blocks whose dependencies
+//   have started (ties: first ready first).  It waits even less, but costs
+//   a footprint scan per block on the host; on the 16-frame 1080p batch it
+//   saved 0.47 ms of a 17.9 ms kernel for 1.6 ms more host time than the
+//   height order.
+
 //
 // Host code, integers only.
 #include <algorithm>
 #include <cstdint>
-#include <queue>
 #include <vector>
 
 #include "../../include/fse.h"
@@ -30,36 +34,42 @@
 namespace fse {
 
 void frame_depths(FrameDepths &f, int rad) {
-    const int nb = f.bw * f.bh;
-    f.level.assign(nb, -1);
-    f.height.assign(nb, 0);
-    f.indeg.assign(nb, 0);
-    f.pos.assign(nb, -1);
-    const int32_t *gob = f.gob;
-    for (int j = 0; j < f.n; ++j) {  // increasing group
-        const int b = f.ids[j], by = b / f.bw, bx = b - by * f.bw, g = gob[b];
+    f.rad = rad;
+    f.pw = f.bw + 2 * rad;
+    const int ph = f.bh + 2 * rad;
+    f.gp.assign((size_t)f.pw * ph, -1);
+    for (int y = 0; y < f.bh; ++y)
+        std::copy(f.gob + (size_t)y * f.bw, f.gob + (size_t)(y + 1) * f.bw,
+                  f.gp.begin() + (size_t)(y + rad) * f.pw + rad);
+    f.nbr.clear();
+    for (int dy = -rad; dy <= rad; ++dy)
+        for (int dx = -rad; dx <= rad; ++dx)
+            if (dy || dx) f.nbr.push_back(dy * f.pw + dx);
+    f.level.assign(f.gp.size(), 0);
+    f.height.assign(f.gp.size(), 0);
+    f.indeg.assign(f.gp.size(), 0);
+    f.pid.resize(f.n);
+    const int32_t *gp = f.gp.data();
+    for (int j = 0; j < f.n; ++j) {  // increasing group: dependencies first
+        const int b = f.ids[j], by = b / f.bw, bx = b - by * f.bw;
+        const int p = (by + rad) * f.pw + bx + rad;
+        const uint32_t g = (uint32_t)gp[p];
         int lv = 0, deg = 0;
-        for (int y = std::max(0, by - rad); y <= std::min(f.bh - 1, by + rad); ++y)
-            for (int x = std::max(0, bx - rad); x <= std::min(f.bw - 1, bx + rad); ++x) {
-                const int d = y * f.bw + x;
-                if (gob[d] >= 0 && gob[d] < g) {
-                    lv = std::max(lv, f.level[d] + 1);
-                    ++deg;
-                }
-            }
-        f.level[b] = lv;
-        f.indeg[b] = deg;
-        f.pos[b] = j;
+        for (const int32_t o : f.nbr) {  // branch-free: the tests are unpredictable
+            const int dep = (uint32_t)gp[p + o] < g;  // 0 <= group < g (-1 wraps high)
+            lv = std::max(lv, dep * (f.level[p + o] + 1));
+            deg += dep;
+        }
+        f.pid[j] = p;
+        f.level[p] = lv;
+        f.indeg[p] = deg;
     }
     for (int j = f.n - 1; j >= 0; --j) {  // decreasing group: dependants first
-        const int b = f.ids[j], by = b / f.bw, bx = b - by * f.bw, g = gob[b];
+        const int p = f.pid[j], g = gp[p];
         int h = 1;
-        for (int y = std::max(0, by - rad); y <= std::min(f.bh - 1, by + rad); ++y)
-            for (int x = std::max(0, bx - rad); x <= std::min(f.bw - 1, bx + rad); ++x) {
-                const int s = y * f.bw + x;
-                if (gob[s] > g) h = std::max(h, f.height[s] + 1);
-            }
-        f.height[b] = h;
+        for (const int32_t o : f.nbr)
+            h = std::max(h, (gp[p + o] > g) * (f.height[p + o] + 1));
+        f.height[p] = h;
     }
 }
 
@@ -69,70 +79,91 @@ void level_claims(const std::vector<FrameDepths> &frames, std::vector<int2> &ite
     size_t total = 0;
     for (const FrameDepths &f : frames) {
         total += f.n;
-        for (int j = 0; j < f.n; ++j) n_levels = std::max(n_levels, f.level[f.ids[j]] + 1);
+        for (int j = 0; j < f.n; ++j) n_levels = std::max(n_levels, f.level[f.pid[j]] + 1);
     }
     // counting sort by level; within a level by frame, then group order
     level_start.assign(n_levels + 1, 0);
     for (const FrameDepths &f : frames)
-        for (int j = 0; j < f.n; ++j) ++level_start[f.level[f.ids[j]] + 1];
+        for (int j = 0; j < f.n; ++j) ++level_start[f.level[f.pid[j]] + 1];
     for (int l = 0; l < n_levels; ++l) level_start[l + 1] += level_start[l];
     std::vector<int> fill(level_start.begin(), level_start.end() - 1);
     items.assign(total, make_int2(0, 0));
     for (size_t i = 0; i < frames.size(); ++i) {
         const FrameDepths &f = frames[i];
-        for (int j = 0; j < f.n; ++j) {
-            const int b = f.ids[j];
-            items[fill[f.level[b]]++] = make_int2((int)i, b);
-        }
+        for (int j = 0; j < f.n; ++j)
+            items[fill[f.level[f.pid[j]]]++] = make_int2((int)i, f.ids[j]);
     }
 }
 
-namespace {
-
-struct Ready {
-    int32_t h, frame, pos, block;
-    // priority: longer chain, then earlier frame, then earlier in group order
-    bool operator<(const Ready &o) const {
-        if (h != o.h) return h < o.h;
-        if (frame != o.frame) return frame > o.frame;
-        return pos > o.pos;
-    }
-};
-
-}  // namespace
-
-void schedule_claims(std::vector<FrameDepths> &frames, int rad, int workers,
-                     std::vector<int2> &items) {
-    std::priority_queue<Ready> ready;
+void height_claims(const std::vector<FrameDepths> &frames, std::vector<int2> &items) {
+    int max_h = 0;
     size_t total = 0;
-    for (size_t i = 0; i < frames.size(); ++i) {
-        FrameDepths &f = frames[i];
+    for (const FrameDepths &f : frames) {
         total += f.n;
+        for (int j = 0; j < f.n; ++j) max_h = std::max(max_h, f.height[f.pid[j]]);
+    }
+    // counting sort by height, descending; within a height by frame, then
+    // group order
+    std::vector<size_t> start(max_h + 2, 0);
+    for (const FrameDepths &f : frames)
+        for (int j = 0; j < f.n; ++j) ++start[max_h - f.height[f.pid[j]] + 1];
+    for (int h = 0; h <= max_h; ++h) start[h + 1] += start[h];
+    items.assign(total, make_int2(0, 0));
+    for (size_t i = 0; i < frames.size(); ++i) {
+        const FrameDepths &f = frames[i];
+        for (int j = 0; j < f.n; ++j)
+            items[start[max_h - f.height[f.pid[j]]]++] = make_int2((int)i, f.ids[j]);
+    }
+}
+
+void schedule_claims(std::vector<FrameDepths> &frames, int workers, std::vector<int2> &items) {
+    // Ready blocks in buckets by height (the longest chain first); a bucket
+    // is a FIFO of (frame, padded cell): initially frame by frame in group
+    // order, then in the order of release.  Heights are at most the number
+    // of groups of a frame.
+    int max_h = 0;
+    size_t total = 0;
+    for (const FrameDepths &f : frames) {
+        total += f.n;
+        for (int j = 0; j < f.n; ++j) max_h = std::max(max_h, f.height[f.pid[j]]);
+    }
+    std::vector<std::vector<int2>> bucket(max_h + 1);
+    std::vector<size_t> head(max_h + 1, 0);
+    for (size_t i = 0; i < frames.size(); ++i) {
+        const FrameDepths &f = frames[i];
         for (int j = 0; j < f.n; ++j) {
-            const int b = f.ids[j];
-            if (f.indeg[b] == 0) ready.push(Ready{f.height[b], (int32_t)i, j, b});
+            const int p = f.pid[j];
+            if (f.indeg[p] == 0) bucket[f.height[p]].push_back(make_int2((int)i, p));
         }
     }
     items.clear();
     items.reserve(total);
     const size_t P = (size_t)std::max(workers, 1);
-    std::vector<Ready> released;
-    while (!ready.empty()) {
+    std::vector<int2> released;
+    int top = max_h;  // no ready block is higher
+    while (items.size() < total) {
         released.clear();
-        for (size_t t = 0; t < P && !ready.empty(); ++t) {
-            const Ready r = ready.top();
-            ready.pop();
-            items.push_back(make_int2(r.frame, r.block));
-            FrameDepths &f = frames[r.frame];
-            const int by = r.block / f.bw, bx = r.block - by * f.bw, g = f.gob[r.block];
-            for (int y = std::max(0, by - rad); y <= std::min(f.bh - 1, by + rad); ++y)
-                for (int x = std::max(0, bx - rad); x <= std::min(f.bw - 1, bx + rad); ++x) {
-                    const int s = y * f.bw + x;
-                    if (f.gob[s] > g && --f.indeg[s] == 0)
-                        released.push_back(Ready{f.height[s], r.frame, f.pos[s], s});
-                }
+        for (size_t t = 0; t < P; ++t) {
+            while (top > 0 && head[top] == bucket[top].size()) --top;
+            if (head[top] == bucket[top].size()) break;  // nothing ready
+            const int2 it = bucket[top][head[top]++];
+            FrameDepths &f = frames[it.x];
+            items.push_back(make_int2(it.x, f.block_of(it.y)));
+            const int g = f.gp[it.y];
+            for (const int32_t o : f.nbr) {
+                const int q = it.y + o;
+                const int dep = f.gp[q] > g;  // q waits for this block
+                f.indeg[q] -= dep;
+                if (dep & (f.indeg[q] == 0)) released.push_back(make_int2(it.x, q));
+            }
         }
-        for (const Ready &r : released) ready.push(r);
+        if (released.empty() && head[top] == bucket[top].size())
+            break;  // nothing left to start (all blocks were, for a consistent plan)
+        for (const int2 &r : released) {
+            const int h = frames[r.x].height[r.y];
+            bucket[h].push_back(r);
+            top = std::max(top, h);
+        }
     }
 }
 
@@ -143,9 +174,8 @@ extern "C" int fse_plan_claims(int n_frames, const int32_t *bw, const int32_t *b
                                int32_t *items, int32_t *level_start, int32_t *n_levels) {
     using namespace fse;
     const int lb = block_log2(block);
-    if (n_frames <= 0 || !bw || !bh || !group_of_block || !items || lb < 0 ||
-        (mode != 0 && mode != 1) || (mode == 0 && (!level_start || !n_levels)) ||
-        (mode == 1 && workers <= 0))
+    if (n_frames <= 0 || !bw || !bh || !group_of_block || !items || lb < 0 || mode < 0 ||
+        mode > 2 || (mode == 0 && (!level_start || !n_levels)) || (mode == 1 && workers <= 0))
         return FSE_EINVAL;
     std::vector<FrameDepths> frames(n_frames);
     size_t off = 0;
@@ -173,8 +203,10 @@ extern "C" int fse_plan_claims(int n_frames, const int32_t *bw, const int32_t *b
         level_claims(frames, out, ls);
         *n_levels = (int32_t)ls.size() - 1;
         for (size_t l = 0; l < ls.size(); ++l) level_start[l] = ls[l];
+    } else if (mode == 1) {
+        schedule_claims(frames, workers, out);
     } else {
-        schedule_claims(frames, kBorder >> lb, workers, out);
+        height_claims(frames, out);
     }
     for (size_t k = 0; k < out.size(); ++k) {
         items[2 * k] = out[k].x;

@@ -63,34 +63,55 @@ def test_levels_are_independent_sets_in_dependency_order(B):
 
 
 def _list_schedule(maps, rad, P):
-    """Rounds of P starts, ready blocks by (longest chain of dependants,
-    frame, group order), dependants ready in the next round."""
+    """Rounds of up to P starts; ready blocks by longest chain of dependants,
+    ties first-ready-first (initially frame by frame in group order, then in
+    order of release, neighbours scanned row by row); dependants of a round
+    become ready in the next one."""
     deps = [_deps(g, rad) for g in maps]
-    succ, indeg, height, pos = {}, {}, {}, {}
+    indeg, height = {}, {}
+    buckets = {}
     for f, g in enumerate(maps):
-        order = sorted(deps[f], key=lambda b: (g.ravel()[b], b))
-        for j, b in enumerate(order):
-            pos[(f, b)] = j
+        bh, bw = g.shape
+        gf = g.ravel()
+        order = sorted(deps[f], key=lambda b: (gf[b], b))
+        for b in order:
             indeg[(f, b)] = len(deps[f][b])
-            for d in deps[f][b]:
-                succ.setdefault((f, d), []).append((f, b))
         for b in reversed(order):
-            height[(f, b)] = 1 + max((height[s] for s in succ.get((f, b), [])), default=0)
-    ready = [(-height[k], k[0], pos[k], k) for k in indeg if indeg[k] == 0]
-    heapq.heapify(ready)
+            by, bx = divmod(b, bw)
+            h = 1
+            for y in range(max(0, by - rad), min(bh, by + rad + 1)):
+                for x in range(max(0, bx - rad), min(bw, bx + rad + 1)):
+                    s = y * bw + x
+                    if gf[s] > gf[b]:
+                        h = max(h, height[(f, s)] + 1)
+            height[(f, b)] = h
+        for b in order:
+            if indeg[(f, b)] == 0:
+                buckets.setdefault(height[(f, b)], []).append((f, b))
     out = []
-    while ready:
+    while True:
         rel = []
-        for _ in range(min(P, len(ready))):
-            *_, k = heapq.heappop(ready)
-            out.append(k)
-            for s in succ.get(k, []):
-                indeg[s] -= 1
-                if indeg[s] == 0:
-                    rel.append(s)
-        for s in rel:
-            heapq.heappush(ready, (-height[s], s[0], pos[s], s))
-    return out
+        for _ in range(P):
+            ready = [h for h, q in buckets.items() if q]
+            if not ready:
+                break
+            f, b = buckets[max(ready)].pop(0)
+            out.append((f, b))
+            g = maps[f]
+            bh, bw = g.shape
+            gf = g.ravel()
+            by, bx = divmod(b, bw)
+            for y in range(max(0, by - rad), min(bh, by + rad + 1)):
+                for x in range(max(0, bx - rad), min(bw, bx + rad + 1)):
+                    s = y * bw + x
+                    if gf[s] > gf[b]:
+                        indeg[(f, s)] -= 1
+                        if indeg[(f, s)] == 0:
+                            rel.append((f, s))
+        if not rel and not any(buckets.values()):
+            return out
+        for k in rel:
+            buckets.setdefault(height[k], []).append(k)
 
 
 @pytest.mark.parametrize("B,P", [(16, 5), (16, 64), (8, 7), (2, 16)])
@@ -133,6 +154,43 @@ def test_invalid_arguments():
     with pytest.raises(fse.FseError):
         fse.fse_plan_claims([gob], block=3)
     with pytest.raises(fse.FseError):
-        fse.fse_plan_claims([gob], mode=2)
+        fse.fse_plan_claims([gob], mode=3)
     with pytest.raises(fse.FseError):
         fse.fse_plan_claims([gob], mode=1, workers=0)
+
+
+def _heights(gob, rad):
+    bh, bw = gob.shape
+    gf = gob.ravel()
+    order = sorted(np.flatnonzero(gf >= 0), key=lambda b: (gf[b], b))
+    h = {}
+    for b in reversed(order):
+        by, bx = divmod(int(b), bw)
+        v = 1
+        for y in range(max(0, by - rad), min(bh, by + rad + 1)):
+            for x in range(max(0, bx - rad), min(bw, bx + rad + 1)):
+                s = y * bw + x
+                if gf[s] > gf[b]:
+                    v = max(v, h[s] + 1)
+        h[int(b)] = v
+    return h, order
+
+
+@pytest.mark.parametrize("B", [16, 4])
+def test_height_order_is_topological_longest_chain_first(B):
+    rad = 16 // B
+    maps = _frames(40 + B, n=3, bh=8, bw=12)
+    items, ls = fse.fse_plan_claims(maps, block=B, mode=2)
+    assert ls is None
+    want = []
+    for f, g in enumerate(maps):
+        h, order = _heights(g, rad)
+        want += [(-h[b], f, j, int(b)) for j, b in enumerate(order)]
+    want.sort()
+    assert [tuple(t) for t in items.tolist()] == [(f, b) for _, f, _, b in want]
+    # dependencies first
+    deps = [_deps(g, rad) for g in maps]
+    seen = set()
+    for f, b in items.tolist():
+        assert all((f, d) in seen for d in deps[f][b])
+        seen.add((f, b))
