@@ -60,17 +60,14 @@ static bool encode_map(CUtensorMap *map, CUtensorMapDataType type, const void *b
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// The luma, loss-mask and working-frame maps of a frame.  False when a
-// buffer or row pitch is not 16-byte aligned (the frame is then gathered
-// with plain loads).
+// The luma and loss-mask maps of a frame.  False when a buffer or the row
+// pitch is not 16-byte aligned (the frame is then gathered with plain loads).
 static bool encode_frame_maps(const FrameDesc &d, CUtensorMap *maps) {
     static_assert(sizeof(CUtensorMap) == kTensorMapBytes, "tensor map size");
     return encode_map(&maps[0], CU_TENSOR_MAP_DATA_TYPE_UINT8, d.luma, d.W, d.H,
                       (size_t)d.stride) &&
            encode_map(&maps[1], CU_TENSOR_MAP_DATA_TYPE_UINT8, d.mask, d.W, d.H,
-                      (size_t)d.stride) &&
-           encode_map(&maps[2], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, d.work, d.W, d.H,
-                      (size_t)d.wstride * sizeof(float));
+                      (size_t)d.stride);
 }
 
 // ---------------------------------------------------------------------------

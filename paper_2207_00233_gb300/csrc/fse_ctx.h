@@ -30,7 +30,7 @@ struct HostBuf {
 // Everything one in-flight batch needs on the device.
 struct Workspace {
     DevBuf frames, work, lost, lost_off, gob, items, done, status, trace;
-    DevBuf tmaps;                  // TMA descriptors of the frames (3 per frame)
+    DevBuf tmaps;                  // TMA descriptors of the frames (2 per frame)
     DevBuf d_luma, d_mask, d_out;  // device copies of host frames
     HostBuf stage;                 // pinned staging for uploads / readback
     HostBuf io;                    // pinned staging of serving frames

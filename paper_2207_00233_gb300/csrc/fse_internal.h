@@ -92,23 +92,23 @@ constexpr int kYOff = 2 * kArea * kTileStride * 4;                 // after the 
 constexpr int kR0Off = kYOff + kYRows * kYStride * 4;              // 64 x 33 float2
 static_assert(kR0Off + kDft * kHalfCols * 8 <= kW4Bytes, "projection scratch overflow");
 
-// TMA staging of a frame area, before the gather: the luma, loss-mask and
-// working-frame tiles of 48 x 48 samples, starting at the sample row of the
-// area and at the 16-byte boundary at or below its first column (the copy
-// must start on a 16-byte boundary).  With the 16-sample frame the area's
-// first column is at most 14 samples past that boundary and M = B + 32
-// <= 34 + 14 for B < 16, so 48 columns always cover it.  The tiles share the
-// (not yet used) projection scratch at kYOff.
+// TMA staging of a frame area, before the gather: the luma and loss-mask
+// tiles of 48 x 48 samples, starting at the sample row of the area and at
+// the 16-byte boundary at or below its first column (the copy must start on
+// a 16-byte boundary).  With the 16-sample frame the area's first column is
+// at most 14 samples past that boundary and M = B + 32 <= 34 + 14 for
+// B < 16, so 48 columns always cover it.  The tiles share the (not yet
+// used) projection scratch at kYOff.  Samples of the working frame are read
+// only where the area holds concealed samples (class R), with plain loads.
 constexpr int kStageCols = 48, kStageRows = 48;
 constexpr int kStageLumaOff = kYOff;
 constexpr int kStageMaskOff = kStageLumaOff + kStageCols * kStageRows;
-constexpr int kStageWorkOff = kStageMaskOff + kStageCols * kStageRows;
-constexpr int kStageBytes = kStageCols * kStageRows * (1 + 1 + 4);  // 13824
-static_assert(kStageLumaOff % 128 == 0 && kStageMaskOff % 128 == 0 && kStageWorkOff % 128 == 0,
+constexpr int kStageBytes = kStageCols * kStageRows * 2;  // 4608
+static_assert(kStageLumaOff % 128 == 0 && kStageMaskOff % 128 == 0,
               "TMA destinations must be 128-byte aligned");
-static_assert(kStageWorkOff + kStageCols * kStageRows * 4 <= kW4Bytes, "staging overflow");
+static_assert(kStageMaskOff + kStageCols * kStageRows <= kW4Bytes, "staging overflow");
 constexpr int kTensorMapBytes = 128;       // one CUtensorMap
-constexpr int kMapsPerFrame = 3;           // luma, mask, working frame
+constexpr int kMapsPerFrame = 2;           // luma, mask
 size_t frag_bytes(int precision);
 cudaError_t launch_build_frags(int precision, const float2 *tw, uint4 *out,
                                cudaStream_t stream);
@@ -125,8 +125,8 @@ struct FrameDesc {
     uint32_t *done;          // [bh*bw] completion flags (persistent executor)
     int lb;                  // log2 of the block size B (1..4)
     int pad0;
-    const void *tmaps;       // 3 tensor maps (luma, mask, work), 64-byte
-                             // aligned, or null: gather with plain loads
+    const void *tmaps;       // 2 tensor maps (luma, mask), 64-byte aligned,
+                             // or null: gather with plain loads
 };
 
 // Work of the persistent executor: items are (frame, block) pairs in a claim

@@ -129,21 +129,17 @@ struct FrameSrc {
         : fd(f), by(block / f.bw), bx(block % f.bw), self(block), gself(f.gob[block]),
           stage(st) {}
 
-    // Class and weight of area sample (m, n) at frame position (y, x), given
-    // its loss flag, luma and working-frame value.
-    __device__ __forceinline__ void classify(int y, int x, bool lost, float luma, float work,
-                                             float rho, float delta, float &w, float &v) const {
-        if (!lost) {
-            w = rho;
-            v = luma;
-        } else {
-            const int cb = (y >> fd.lb) * fd.bw + (x >> fd.lb);
-            if (cb != self) {
-                const int gc = fd.gob[cb];
-                if (gc >= 0 && gc < gself) {
-                    w = delta * rho;
-                    v = work;
-                }
+    // Class and weight of the lost area sample at frame position (y, x):
+    // R (an earlier-group block's concealed sample, read from the working
+    // frame) or weight 0.
+    __device__ __forceinline__ void classify_lost(int y, int x, float rho, float delta, float &w,
+                                                  float &v) const {
+        const int cb = (y >> fd.lb) * fd.bw + (x >> fd.lb);
+        if (cb != self) {
+            const int gc = fd.gob[cb];
+            if (gc >= 0 && gc < gself) {
+                w = delta * rho;
+                v = __ldcg(fd.work + (size_t)y * fd.wstride + x);
             }
         }
     }
@@ -156,15 +152,18 @@ struct FrameSrc {
             const int dx = x0 - (x0 & ~15);
             const uint8_t *sl = stage;
             const uint8_t *sm = stage + (kStageMaskOff - kStageLumaOff);
-            const float *sw = reinterpret_cast<const float *>(stage + (kStageWorkOff - kStageLumaOff));
             for (int p = threadIdx.x; p < kArea * kArea; p += kThreads) {
                 const int m = p / kArea, n = p - m * kArea;
                 const int y = y0 + m, x = x0 + n;
                 float w = 0.f, v = 0.f;
                 if (m < M && n < M && y >= 0 && y < fd.H && x >= 0 && x < fd.W) {
                     const int q = m * kStageCols + n + dx;
-                    const bool lost = sm[q] != 0;
-                    classify(y, x, lost, (float)sl[q], lost ? sw[q] : 0.f, rho_tab[p], delta, w, v);
+                    if (!sm[q]) {
+                        w = rho_tab[p];
+                        v = (float)sl[q];
+                    } else {
+                        classify_lost(y, x, rho_tab[p], delta, w, v);
+                    }
                 }
                 xt[m * kTileStride + n] = w * v;
                 wt[m * kTileStride + n] = w;
@@ -177,19 +176,11 @@ struct FrameSrc {
             float w = 0.f, v = 0.f;
             if (m < M && n < M && y >= 0 && y < fd.H && x >= 0 && x < fd.W) {
                 const size_t q = (size_t)y * fd.stride + x;
-                const bool lost = fd.mask[q] != 0;
-                if (!lost) {
+                if (!fd.mask[q]) {
                     w = rho_tab[p];
                     v = (float)fd.luma[q];
                 } else {
-                    const int cb = (y >> fd.lb) * fd.bw + (x >> fd.lb);
-                    if (cb != self) {
-                        const int gc = fd.gob[cb];
-                        if (gc >= 0 && gc < gself) {
-                            w = delta * rho_tab[p];
-                            v = __ldcg(fd.work + (size_t)y * fd.wstride + x);
-                        }
-                    }
+                    classify_lost(y, x, rho_tab[p], delta, w, v);
                 }
             }
             xt[m * kTileStride + n] = w * v;
@@ -208,8 +199,6 @@ struct FrameSrc {
         const float v = fminf(fmaxf(g, 0.f), 255.f);
         fd.work[(size_t)y * fd.wstride + x] = v;
         fd.out[q] = (uint8_t)__float2int_rn(v);
-        // later blocks read this sample with TMA (async proxy)
-        asm volatile("fence.proxy.async.global;" ::: "memory");
     }
 };
 
@@ -1007,8 +996,8 @@ __device__ __forceinline__ void stage_init(unsigned char *smem) {
     }
 }
 
-// Stages the luma, mask and working-frame tiles of the area of `block` with
-// three TMA copies completing on the CTA's mbarrier.  Returns false on every
+// Stages the luma and mask tiles of the area of `block` with two TMA copies
+// completing on the CTA's mbarrier.  Returns false on every
 // thread when the copies did not complete within kStageLimitNs; the caller
 // then leaves the kernel.
 __device__ __forceinline__ bool stage_area(const FrameDesc &fd, int block, unsigned char *smem) {
@@ -1019,15 +1008,14 @@ __device__ __forceinline__ bool stage_area(const FrameDesc &fd, int block, unsig
         const int B = 1 << fd.lb, by = block / fd.bw, bx = block - by * fd.bw;
         const int y0 = by * B - kBorder, xs = (bx * B - kBorder) & ~15;
         const unsigned char *maps = static_cast<const unsigned char *>(fd.tmaps);
-        // Order the CTA's earlier accesses to the staging region (previous
-        // block) and the frame samples published by earlier blocks before
-        // the copies.
+        // Order the CTA's earlier generic accesses to the staging region
+        // (previous block) before the copies.  (The kernel never writes the
+        // staged samples that it uses: an `out` aliasing `luma` changes lost
+        // samples only, whose luma is not read.)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("fence.proxy.async.global;" ::: "memory");
         mbar_arrive_expect_tx(bar, kStageBytes);
         tma_load_2d(smem_addr(smem + kStageLumaOff), maps, xs, y0, bar);
         tma_load_2d(smem_addr(smem + kStageMaskOff), maps + kTensorMapBytes, xs, y0, bar);
-        tma_load_2d(smem_addr(smem + kStageWorkOff), maps + 2 * kTensorMapBytes, xs, y0, bar);
     }
     const bool ok = __syncthreads_and(mbar_wait(bar, ph, kStageLimitNs));
     if (!ok) mbar_wait(bar, ph, kStageLimitNs);  // copies in flight land before leaving
