@@ -439,7 +439,7 @@ def main():
     h2d = sum(img.nbytes + mask.nbytes for img, mask in frames)
     d2h = sum(img.nbytes for img, _ in frames)
 
-    # ---- plain path: one frame per call, one launch per group ----
+    # ---- plain path: one frame per call, one launch per dependency level ----
     plain = None
     if not args.no_plain:
         pp = fse.make_params(iters=K_ITERS, order=fse.FSE_ORDER_OPTIMIZED,
@@ -505,7 +505,7 @@ def main():
             "clocks": clk,
             "plain_path": None if plain is None else {
                 "value": plain, "unit": UNIT,
-                "what": "same frames, one fse_conceal_batch call per frame, one launch per group"},
+                "what": "same frames, one fse_conceal_batch call per frame, one launch per dependency level"},
         }
         if base is not None:
             line["cpu_baseline"] = base

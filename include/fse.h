@@ -72,7 +72,8 @@ extern "C" {
 #define FSE_PREC_TF32X3 5      /* split-TF32 operands, FP32-grade accuracy    */
 
 /* How the groups are dispatched on the device. */
-#define FSE_EXEC_GROUPS 0      /* one launch per group (plain path)              */
+#define FSE_EXEC_GROUPS 0      /* one launch per dependency level (blocks of a
+                                  level are independent; plain path)           */
 #define FSE_EXEC_PERSISTENT 1  /* one persistent launch over all frames; a block
                                   starts once every earlier-group block whose
                                   samples lie in its area has published its

@@ -3,7 +3,7 @@ cannot call cudaMalloc (device memory owned by a host application's pool or
 budget).  Its scratch is one fixed device array inside the library; the test
 calls it through the C-ABI twice in a row, on two different frames, and
 checks each result against the regular entry point fse_conceal_batch run
-with the same parameters (one launch per group, FP32), within the pixel
+with the same parameters (groups executor, FP32), within the pixel
 tolerance of the parity tests.  It also checks the size limit.
 
 Collected last on purpose: a run that stops at the first failure has run
