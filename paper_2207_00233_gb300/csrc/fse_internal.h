@@ -58,10 +58,12 @@ static_assert(kYwOff + kArea * kHalfCols * 8 <= kW4Bytes, "scratch overflow");
 constexpr int kTswOff = kYwOff + kArea * kHalfCols * 8;         // 44160
 static_assert(kTswOff + 33 * 132 * 4 <= kW4Bytes, "column-DFT scratch overflow");
 // After the iterations the W4 region holds the synthesis tables, in chunks
-// of kSynChunk iterations: P[it][i] = dc_it exp(+j 2 pi u_m (16+i) / 64) and
-// E[it][j] = exp(+j 2 pi u_n (16+j) / 64), 16 complex values each.
-constexpr int kSynChunk = 256;
-static_assert(kSynChunk * 32 * 8 <= kW4Bytes, "synthesis tables overflow");
+// of kSynChunk iterations: P[it][i] = dc_it exp(+j 2 pi u_m (16+i) / 64) as
+// (Re, Re, -Im, -Im) and E[it][j] = exp(+j 2 pi u_n (16+j) / 64) as 16 real
+// then 16 imaginary parts; then the partial sums of the samples.
+constexpr int kSynChunk = 128;
+constexpr int kSynPartOff = kSynChunk * 16 * 16 + kSynChunk * 32 * 4;
+static_assert(kSynPartOff + 2 * 128 * 8 <= kW4Bytes, "synthesis tables overflow");
 
 struct KParams {
     float rho, delta, gamma;

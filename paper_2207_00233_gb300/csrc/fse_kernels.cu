@@ -48,6 +48,16 @@ __device__ __forceinline__ u64 mul2(u64 a, u64 b) {
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
+    u64 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 // |R|^2 of a pair; the same instruction sequence is used wherever an
 // energy is compared, so equal inputs give bit-identical energies.
 __device__ __forceinline__ u64 energy2(u64 re, u64 im) {
@@ -938,11 +948,14 @@ __device__ __forceinline__ float run_block(const Src &src, const KParams &kp,
     // with m = 16 + i, n = 16 + j; the exponential factorises, so per chunk
     // of iterations the tables P[it][i] = dc_it exp(+j 2 pi u_m m / 64) and
     // E[it][j] = exp(+j 2 pi u_n n / 64) are built in the (now free) W4
-    // region.  Compensated (Kahan) summation in FP32.
-    const int si = tid >> 4, sj = tid & 15;
-    float2 *ptab = reinterpret_cast<float2 *>(smem);
-    float2 *etab = ptab + kSynChunk * 16;
-    float s = 0.f, c = 0.f;
+    // region.  Thread t sums the sample pair (i, j), (i, j + 1) with
+    // i = (t & 127) >> 3, j = 2 (t & 7) over the iterations of parity t >> 7,
+    // in packed f32x2 compensated (Kahan) sums; the two partial sums of each
+    // sample are then added.
+    u64 *ptab = reinterpret_cast<u64 *>(smem);  // [it][i]: (Re P, Re P), (-Im P, -Im P)
+    float *etab = reinterpret_cast<float *>(smem + kSynChunk * 16 * 16);  // [it]: Re E[16], Im E[16]
+    const int half = tid >> 7, pair = tid & 127, pi = pair >> 3, pj = 2 * (pair & 7);
+    u64 s2 = 0ull, c2 = 0ull;
     for (int c0 = 0; c0 < K; c0 += kSynChunk) {
         const int nc = min(kSynChunk, K - c0);
         for (int e = tid; e < nc * 32; e += kThreads) {
@@ -951,25 +964,36 @@ __device__ __forceinline__ float run_block(const Src &src, const KParams &kp,
             if (q < 16) {
                 const float2 d = dcl[c0 + it];
                 const float2 cs = tw[((u >> 6) * (kBorder + q)) & (kDft - 1)];
-                ptab[it * 16 + q] =
-                    make_float2(fmaf(d.x, cs.x, -d.y * cs.y), fmaf(d.x, cs.y, d.y * cs.x));
+                const float pr = fmaf(d.x, cs.x, -d.y * cs.y), pim = fmaf(d.x, cs.y, d.y * cs.x);
+                ptab[(it * 16 + q) * 2] = pack2(pr, pr);
+                ptab[(it * 16 + q) * 2 + 1] = pack2(-pim, -pim);
             } else {
-                etab[it * 16 + (q - 16)] = tw[((u & 63) * (kBorder + q - 16)) & (kDft - 1)];
+                const float2 ev = tw[((u & 63) * (kBorder + q - 16)) & (kDft - 1)];
+                etab[it * 32 + (q - 16)] = ev.x;
+                etab[it * 32 + q] = ev.y;
             }
         }
         __syncthreads();
-        for (int it = 0; it < nc; ++it) {
-            const float2 pv = ptab[it * 16 + si];
-            const float2 ev = etab[it * 16 + sj];
-            const float term = fmaf(pv.x, ev.x, -pv.y * ev.y);
-            const float yv = term - c;
-            const float t = s + yv;
-            c = (t - s) - yv;
-            s = t;
+        const uint32_t pbase = smem_addr(ptab) + (uint32_t)pi * 16u;
+        for (int it = half; it < nc; it += 2) {
+            u64 pr2, pim2;
+            lds_pair(pbase + (uint32_t)it * 256u, pr2, pim2);
+            const u64 er = *reinterpret_cast<const u64 *>(etab + it * 32 + pj);
+            const u64 ei = *reinterpret_cast<const u64 *>(etab + it * 32 + 16 + pj);
+            const u64 term = fma2(pim2, ei, mul2(pr2, er));  // Re P Re E - Im P Im E
+            const u64 yv = sub2(term, c2);
+            const u64 t = add2(s2, yv);
+            c2 = sub2(sub2(t, s2), yv);
+            s2 = t;
         }
         __syncthreads();
     }
-    return s;
+    float2 *part = reinterpret_cast<float2 *>(smem + kSynPartOff);  // [2][128]
+    part[half * 128 + pair] = unpack2(sub2(s2, c2));
+    __syncthreads();
+    const int q = (tid >> 4) * 8 + ((tid & 15) >> 1);
+    const float2 a = part[q], b = part[128 + q];
+    return (tid & 1) ? a.y + b.y : a.x + b.x;
 }
 
 // ---- kernels -------------------------------------------------------------------
