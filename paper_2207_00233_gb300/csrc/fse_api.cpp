@@ -269,6 +269,40 @@ static int check_frame(const fse_frame &f) {
         }                                          \
     } while (0)
 
+// Block-loss map of a host frame: a block is lost when any of its in-image
+// samples is lost (as k_block_loss computes it on the device).
+std::vector<uint8_t> fse::host_block_loss(const fse_frame &f, int B) {
+    const int bh = (f.height + B - 1) / B, bw = (f.width + B - 1) / B;
+    std::vector<uint8_t> lost((size_t)bh * bw, 0);
+    // OR the B rows of a block row together 8 bytes at a time, then test
+    // each block's B bytes of the result.
+    const size_t words = ((size_t)f.width + 7) / 8;
+    std::vector<uint64_t> acc(words);
+    for (int by = 0; by < bh; ++by) {
+        std::fill(acc.begin(), acc.end(), 0ull);
+        const int y1 = std::min(f.height, (by + 1) * B);
+        for (int y = by * B; y < y1; ++y) {
+            const uint8_t *row = f.loss_mask + (size_t)y * f.stride;
+            const size_t full = (size_t)f.width / 8;
+            for (size_t k = 0; k < full; ++k) {
+                uint64_t v;
+                std::memcpy(&v, row + 8 * k, 8);
+                acc[k] |= v;
+            }
+            uint8_t *bytes = reinterpret_cast<uint8_t *>(acc.data());
+            for (int x = (int)(full * 8); x < f.width; ++x) bytes[x] |= row[x];
+        }
+        const uint8_t *bytes = reinterpret_cast<const uint8_t *>(acc.data());
+        for (int bx = 0; bx < bw; ++bx) {
+            const int x0 = bx * B, x1 = std::min(f.width, x0 + B);
+            uint8_t any = 0;
+            for (int x = x0; x < x1; ++x) any |= bytes[x];
+            lost[(size_t)by * bw + bx] = any != 0;
+        }
+    }
+    return lost;
+}
+
 // ---------------------------------------------------------------------------
 // Host worker pool
 // ---------------------------------------------------------------------------
@@ -742,7 +776,11 @@ extern "C" int fse_conceal_batch_host(fse_ctx *ctx, const fse_frame *frames, int
                              cudaMemcpyHostToDevice, stream));
         dev[i] = fse_frame{dl, dout, dm, h.width, h.height, pitch(i)};
     }
-    rc = run_batch(ctx, ws, dev.data(), n, params, stream, nullptr);
+    // The block-loss maps come from the host masks, on the worker threads,
+    // while the copies run; planning then needs no device round trip.
+    std::vector<std::vector<uint8_t>> lost(n);
+    ctx->pool.run(n, [&](int i) { lost[i] = host_block_loss(frames[i], params->block); });
+    rc = run_batch(ctx, ws, dev.data(), n, params, stream, &lost);
     ctx->last_lost_blocks = ws.lost_blocks;
     ctx->last_groups = ws.groups;
     ctx->last_launches = ws.launches;

@@ -143,6 +143,8 @@ struct fse_ctx {
 };
 
 namespace fse {
+// Block-loss map [bh][bw] of a frame in host memory.
+std::vector<uint8_t> host_block_loss(const fse_frame &f, int B);
 int run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
               const fse_params *p, cudaStream_t stream,
               const std::vector<std::vector<uint8_t>> *host_lost);

@@ -39,22 +39,6 @@ size_t frame_bytes(const fse_frame &f) {
     return ((size_t)device_pitch(f) * f.height + 255) & ~(size_t)255;
 }
 
-// Block-loss map of a host frame.
-std::vector<uint8_t> host_block_loss(const fse_frame &f, int B) {
-    const int bh = (f.height + B - 1) / B, bw = (f.width + B - 1) / B;
-    std::vector<uint8_t> lost((size_t)bh * bw, 0);
-    for (int y = 0; y < f.height; ++y) {
-        const uint8_t *row = f.loss_mask + (size_t)y * f.stride;
-        uint8_t *lrow = lost.data() + (size_t)(y / B) * bw;
-        for (int bx = 0; bx < bw; ++bx) {
-            const int x0 = bx * B, x1 = std::min(f.width, x0 + B);
-            uint8_t any = 0;
-            for (int x = x0; x < x1; ++x) any |= row[x];
-            if (any) lrow[bx] = 1;
-        }
-    }
-    return lost;
-}
 
 void finish(fse_ctx *ctx, Slot &s, int status) {
     const auto now = Clock::now();
