@@ -148,13 +148,17 @@ int fse_plan_order(int bw, int bh, const uint8_t *block_lost, int order,
  *   frame by frame in group order, later in order of release); each round
  *   starts up to `workers` ready blocks, whose dependants become ready in
  *   the next round.
- * mode 2 (persistent executor): longest chain of dependants first (height,
- *   counting the block), then frame, then group order; topological because
- *   a block's height exceeds its dependants'.
+ * mode 2: longest chain of dependants first (height, counting the block),
+ *   then frame, then group order; topological because a block's height
+ *   exceeds its dependants'.
+ * mode 3 (persistent executor with `workers` CTAs): the mode-2 order cut
+ *   into rounds of `workers` claims; each block's round is raised to one past
+ *   the latest round of its dependencies (taken in group order); items are
+ *   then sorted by round, within a round by frame, then group order.
  * level_start / n_levels are used in mode 0 only.
  * Output, caller-owned: items [2 * lost blocks] (frame, block) pairs.
  * Errors: FSE_EINVAL on NULL pointers, a dimension <= 0, an unsupported
- * block size, an unknown mode or workers <= 0 in mode 1. */
+ * block size, an unknown mode or workers <= 0 in mode 1 or 3. */
 int fse_plan_claims(int n_frames, const int32_t *bw, const int32_t *bh,
                     const int32_t *group_of_block, int block, int workers, int mode,
                     int32_t *items, int32_t *level_start, int32_t *n_levels);

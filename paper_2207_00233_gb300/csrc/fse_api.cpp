@@ -323,12 +323,20 @@ void fse::WorkerPool::worker() {
         cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
         if (stop_) return;
         seen = gen_;
+        if (!open_) continue;  // woke after the job was finished
+        ++in_job_;
         const std::function<void(int)> *fn = fn_;
         const int n = n_;
         lk.unlock();
-        for (int i = next_.fetch_add(1); i < n; i = next_.fetch_add(1)) (*fn)(i);
+        for (int i = next_.fetch_add(1); i < n; i = next_.fetch_add(1)) {
+            (*fn)(i);
+            if (done_.fetch_add(1) + 1 == n) {
+                std::lock_guard<std::mutex> g(mu_);
+                done_cv_.notify_all();
+            }
+        }
         lk.lock();
-        if (--active_ == 0) done_cv_.notify_one();
+        if (--in_job_ == 0) done_cv_.notify_all();
     }
 }
 
@@ -340,8 +348,10 @@ void fse::WorkerPool::run(int n, const std::function<void(int)> &fn) {
     }
     if (!started_) {
         started_ = true;
+        // a few threads: the jobs are short, and a thread that the OS is
+        // slow to wake only loses its share
         const int hw = (int)std::thread::hardware_concurrency();
-        const int nt = std::min(std::max(hw - 1, 0), 15);
+        const int nt = std::min(std::max(hw - 2, 0), 14);
         try {
             for (int t = 0; t < nt; ++t) threads_.emplace_back([this] { worker(); });
         } catch (...) {  // no threads: the calling thread does the work
@@ -356,13 +366,19 @@ void fse::WorkerPool::run(int n, const std::function<void(int)> &fn) {
         fn_ = &fn;
         n_ = n;
         next_.store(0);
-        active_ = (int)threads_.size();
+        done_.store(0);
+        open_ = true;
         ++gen_;
     }
     cv_.notify_all();
-    for (int i = next_.fetch_add(1); i < n; i = next_.fetch_add(1)) fn(i);
+    for (int i = next_.fetch_add(1); i < n; i = next_.fetch_add(1)) {
+        fn(i);
+        done_.fetch_add(1);
+    }
     std::unique_lock<std::mutex> lk(mu_);
-    done_cv_.wait(lk, [&] { return active_ == 0; });
+    done_cv_.wait(lk, [&] { return done_.load() == n; });
+    open_ = false;  // late workers skip this job
+    done_cv_.wait(lk, [&] { return in_job_ == 0; });
     fn_ = nullptr;
 }
 
@@ -512,7 +528,8 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
     std::vector<int2> items;
     std::vector<int> level_start;
     if (persistent)
-        height_claims(depths, items);
+        delay_claims(depths, std::max(grid, 1), items,
+                     [&](int n, const std::function<void(int)> &fn) { ctx->pool.run(n, fn); });
     else
         level_claims(depths, items, level_start);
     const int n_launch_levels = persistent ? 0 : (int)level_start.size() - 1;

@@ -77,8 +77,9 @@ public:
     WorkerPool &operator=(const WorkerPool &) = delete;
     ~WorkerPool();
     // fn(i) for i in [0, n) on the workers and the calling thread; returns
-    // when all are done.  A call that finds the pool busy (another thread's
-    // batch) runs its jobs on the calling thread.
+    // when all are done.  Workers that have not woken up by then do not
+    // join in (no wait on a descheduled thread).  A call that finds the pool
+    // busy (another thread's batch) runs its jobs on the calling thread.
     void run(int n, const std::function<void(int)> &fn);
 
 private:
@@ -88,10 +89,10 @@ private:
     std::mutex mu_;      // guards the job description below
     std::condition_variable cv_, done_cv_;
     const std::function<void(int)> *fn_ = nullptr;
-    int n_ = 0, active_ = 0;
+    int n_ = 0, in_job_ = 0;  // workers inside the current job
     unsigned gen_ = 0;
-    bool stop_ = false, started_ = false;
-    std::atomic<int> next_{0};
+    bool open_ = false, stop_ = false, started_ = false;
+    std::atomic<int> next_{0}, done_{0};
 };
 
 }  // namespace fse

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -183,6 +184,7 @@ struct FrameDepths {
     std::vector<int32_t> nbr;                   // footprint offsets (no centre)
     std::vector<int32_t> pid;                   // padded cell of ids[j]
     std::vector<int32_t> level, height, indeg;  // per padded cell
+    std::vector<int32_t> key;                   // claim round (delay_claims)
     int block_of(int c) const { return (c / pw - rad) * bw + (c % pw - rad); }
 };
 void frame_depths(FrameDepths &f, int rad);
@@ -191,6 +193,11 @@ void level_claims(const std::vector<FrameDepths> &frames, std::vector<int2> &ite
                   std::vector<int> &level_start);
 // Items by height, descending (persistent executor).
 void height_claims(const std::vector<FrameDepths> &frames, std::vector<int2> &items);
+// Items in the height order cut into rounds of `workers` claims, each block
+// moved to no earlier than the round after its latest dependency's;
+// pfor(n, fn) runs fn(0..n-1), possibly in parallel (one call per frame).
+void delay_claims(std::vector<FrameDepths> &frames, int workers, std::vector<int2> &items,
+                  const std::function<void(int, const std::function<void(int)> &)> &pfor);
 // Items in list-schedule order for `workers` CTAs (consumes indeg).
 void schedule_claims(std::vector<FrameDepths> &frames, int workers, std::vector<int2> &items);
 bool precision_supported(int precision);

@@ -15,6 +15,13 @@
 //   chain of dependants first (the height of a block exceeds that of every
 //   dependant, so the order is topological).  Long chains start early and
 //   do not form a tail; a claim rarely waits.  Static: a counting sort.
+// * Delayed height order, for the persistent executor: the height order cut
+//   into rounds of P claims, each block moved to no earlier than the round
+//   after its latest dependency's (dependencies first, per frame), then
+//   sorted by round (within a round by frame, then group order).  A block
+//   then rarely waits for a dependency claimed just before it; close to the
+//   list schedule below, at the cost of one footprint scan per block, and
+//   every pass runs per frame (in parallel) but for prefix sums.
 // * Schedule (for comparison): list scheduling of P workers with unit
 //   block times, longest chain first among the blocks whose dependencies
 //   have started (ties: first ready first).  It waits even less, but costs
@@ -26,6 +33,7 @@
 // Host code, integers only.
 #include <algorithm>
 #include <cstdint>
+#include <functional>
 #include <vector>
 
 #include "../../include/fse.h"
@@ -95,25 +103,99 @@ void level_claims(const std::vector<FrameDepths> &frames, std::vector<int2> &ite
     }
 }
 
-void height_claims(const std::vector<FrameDepths> &frames, std::vector<int2> &items) {
+namespace {
+
+// (frame, position in the frame's group order) of every lost block, longest
+// chain of dependants first; within a height by frame, then group order.
+void height_order(const std::vector<FrameDepths> &frames, std::vector<int2> &order) {
     int max_h = 0;
     size_t total = 0;
     for (const FrameDepths &f : frames) {
         total += f.n;
         for (int j = 0; j < f.n; ++j) max_h = std::max(max_h, f.height[f.pid[j]]);
     }
-    // counting sort by height, descending; within a height by frame, then
-    // group order
     std::vector<size_t> start(max_h + 2, 0);
     for (const FrameDepths &f : frames)
         for (int j = 0; j < f.n; ++j) ++start[max_h - f.height[f.pid[j]] + 1];
     for (int h = 0; h <= max_h; ++h) start[h + 1] += start[h];
-    items.assign(total, make_int2(0, 0));
+    order.assign(total, make_int2(0, 0));
     for (size_t i = 0; i < frames.size(); ++i) {
         const FrameDepths &f = frames[i];
-        for (int j = 0; j < f.n; ++j)
-            items[start[max_h - f.height[f.pid[j]]]++] = make_int2((int)i, f.ids[j]);
+        for (int j = 0; j < f.n; ++j) order[start[max_h - f.height[f.pid[j]]]++] = make_int2((int)i, j);
     }
+}
+
+}  // namespace
+
+void height_claims(const std::vector<FrameDepths> &frames, std::vector<int2> &items) {
+    height_order(frames, items);
+    for (int2 &it : items) it.y = frames[it.x].ids[it.y];
+}
+
+void delay_claims(std::vector<FrameDepths> &frames, int workers, std::vector<int2> &items,
+                  const std::function<void(int, const std::function<void(int)> &)> &pfor) {
+    const int nf = (int)frames.size();
+    const size_t P = (size_t)std::max(workers, 1);
+    // Per-frame histograms by height; every step below is per frame except
+    // for prefix sums over (height or round, frame).
+    int max_h = 0;
+    for (const FrameDepths &f : frames)
+        for (int j = 0; j < f.n; ++j) max_h = std::max(max_h, f.height[f.pid[j]]);
+    std::vector<std::vector<int32_t>> hist(nf);
+    pfor(nf, [&](int i) {
+        FrameDepths &f = frames[i];
+        hist[i].assign(max_h + 1, 0);
+        for (int j = 0; j < f.n; ++j) ++hist[i][f.height[f.pid[j]]];
+    });
+    // rank of the first block of (height, frame) in the height order
+    // (height descending, then frame, then group order)
+    std::vector<std::vector<size_t>> first(nf, std::vector<size_t>(max_h + 1));
+    size_t pos = 0;
+    for (int h = max_h; h >= 1; --h)
+        for (int i = 0; i < nf; ++i) {
+            first[i][h] = pos;
+            pos += hist[i][h];
+        }
+    // round of each block in the height order, then no earlier than the
+    // round after the latest dependency's (dependencies first: group order)
+    std::vector<int32_t> max_key(nf, 0);
+    pfor(nf, [&](int i) {
+        FrameDepths &f = frames[i];
+        f.key.assign(f.gp.size(), 0);
+        std::vector<size_t> next(first[i]);
+        const int32_t *gp = f.gp.data();
+        int32_t mk = 0;
+        for (int j = 0; j < f.n; ++j) {
+            const int p = f.pid[j];
+            const uint32_t g = (uint32_t)gp[p];
+            int k = (int)(next[f.height[p]]++ / P);
+            for (const int32_t o : f.nbr)
+                if ((uint32_t)gp[p + o] < g) k = std::max(k, f.key[p + o] + 1);
+            f.key[p] = k;
+            mk = std::max(mk, k);
+        }
+        max_key[i] = mk;
+    });
+    // items by round; within a round by frame, then group order
+    int mk = 0;
+    for (int i = 0; i < nf; ++i) mk = std::max(mk, max_key[i]);
+    pfor(nf, [&](int i) {
+        const FrameDepths &f = frames[i];
+        hist[i].assign(mk + 1, 0);
+        for (int j = 0; j < f.n; ++j) ++hist[i][f.key[f.pid[j]]];
+    });
+    pos = 0;
+    for (int k = 0; k <= mk; ++k)
+        for (int i = 0; i < nf; ++i) {
+            const int32_t c = hist[i][k];
+            hist[i][k] = (int32_t)pos;  // now the first slot of (round, frame)
+            pos += c;
+        }
+    items.assign(pos, make_int2(0, 0));
+    pfor(nf, [&](int i) {
+        const FrameDepths &f = frames[i];
+        for (int j = 0; j < f.n; ++j) items[hist[i][f.key[f.pid[j]]]++] = make_int2(i, f.ids[j]);
+    });
 }
 
 void schedule_claims(std::vector<FrameDepths> &frames, int workers, std::vector<int2> &items) {
@@ -175,7 +257,8 @@ extern "C" int fse_plan_claims(int n_frames, const int32_t *bw, const int32_t *b
     using namespace fse;
     const int lb = block_log2(block);
     if (n_frames <= 0 || !bw || !bh || !group_of_block || !items || lb < 0 || mode < 0 ||
-        mode > 2 || (mode == 0 && (!level_start || !n_levels)) || (mode == 1 && workers <= 0))
+        mode > 3 || (mode == 0 && (!level_start || !n_levels)) ||
+        ((mode == 1 || mode == 3) && workers <= 0))
         return FSE_EINVAL;
     std::vector<FrameDepths> frames(n_frames);
     size_t off = 0;
@@ -206,7 +289,12 @@ extern "C" int fse_plan_claims(int n_frames, const int32_t *bw, const int32_t *b
     } else if (mode == 1) {
         schedule_claims(frames, workers, out);
     } else {
-        height_claims(frames, out);
+        if (mode == 2)
+            height_claims(frames, out);
+        else
+            delay_claims(frames, workers, out, [](int n, const std::function<void(int)> &fn) {
+                for (int i = 0; i < n; ++i) fn(i);
+            });
     }
     for (size_t k = 0; k < out.size(); ++k) {
         items[2 * k] = out[k].x;

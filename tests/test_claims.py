@@ -194,3 +194,32 @@ def test_height_order_is_topological_longest_chain_first(B):
     for f, b in items.tolist():
         assert all((f, d) in seen for d in deps[f][b])
         seen.add((f, b))
+
+
+@pytest.mark.parametrize("B,P", [(16, 5), (16, 40), (4, 16)])
+def test_delayed_height_order(B, P):
+    """Mode 3 (the persistent executor's order): the height order in rounds
+    of P claims, each block raised to one past its latest dependency's round,
+    sorted by round, then frame, then group order."""
+    rad = 16 // B
+    maps = _frames(60 + B, n=3, bh=8, bw=12)
+    hitems, _ = fse.fse_plan_claims(maps, block=B, mode=2)
+    items, ls = fse.fse_plan_claims(maps, block=B, workers=P, mode=3)
+    assert ls is None
+    deps = [_deps(g, rad) for g in maps]
+    key = {(int(f), int(b)): pos // P for pos, (f, b) in enumerate(hitems.tolist())}
+    for f, g in enumerate(maps):
+        gf = g.ravel()
+        for b in sorted(deps[f], key=lambda b: (gf[b], b)):
+            key[(f, b)] = max([key[(f, b)]] + [key[(f, d)] + 1 for d in deps[f][b]])
+    gpos = {}
+    for f, g in enumerate(maps):
+        gf = g.ravel()
+        for j, b in enumerate(sorted(np.flatnonzero(gf >= 0), key=lambda b: (gf[b], b))):
+            gpos[(f, int(b))] = j
+    want = sorted((key[k], k[0], gpos[k], k[1]) for k in key)
+    assert [tuple(t) for t in items.tolist()] == [(f, b) for _, f, _, b in want]
+    seen = set()
+    for f, b in items.tolist():
+        assert all((f, d) in seen for d in deps[f][b])
+        seen.add((f, b))
