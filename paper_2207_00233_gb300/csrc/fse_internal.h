@@ -58,6 +58,10 @@ static_assert(kYwOff + kArea * kHalfCols * 8 <= kW4Bytes, "scratch overflow");
 // half spectra.
 constexpr int kTswOff = kYwOff + kArea * kHalfCols * 8;         // 44160
 static_assert(kTswOff + 33 * 132 * 4 <= kW4Bytes, "column-DFT scratch overflow");
+// Row-DFT intermediates (64 planes x 96 rows floats), before the column DFTs
+// reuse the space.
+constexpr int kZsOff = kTswOff;
+static_assert(kZsOff + 64 * 2 * kArea * 4 <= kW4Bytes, "row-DFT scratch overflow");
 // After the iterations the W4 region holds the synthesis tables, in chunks
 // of kSynChunk iterations: P[it][i] = dc_it exp(+j 2 pi u_m (16+i) / 64) as
 // (Re, Re, -Im, -Im) and E[it][j] = exp(+j 2 pi u_n (16+j) / 64) as 16 real

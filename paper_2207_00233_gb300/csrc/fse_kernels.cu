@@ -381,36 +381,73 @@ __device__ __forceinline__ void project_fp32(unsigned char *smem, const float2 *
     float2 *yw = reinterpret_cast<float2 *>(smem + kYwOff);
     const int tid = threadIdx.x;
 
-    // Thread t < 192 owns row m of input t/48 % 2 and the columns
-    // k_n = t/96, t/96 + 2, ..., <= 32.  All lanes of a warp share k_n, so
-    // the twiddle reads are broadcasts, and they read 32 consecutive rows of
-    // one column (conflict-free with the 49-float row stride).
-    if (tid < 2 * 2 * kArea) {
-        const int p = tid % (2 * kArea), which = p / kArea, m = p - which * kArea;
-        const int kn0 = tid / (2 * kArea);
-        const float *row = (which ? wt : xt) + m * kTileStride;
-        constexpr int kCols = (kHalfCols + 1) / 2;  // 17
-        float re[kCols], im[kCols];
+    // Row DFTs of the 96 real rows (w f, then w), split as n = 8a + b and
+    // k_n = r + 8q like the column DFTs:
+    //   Z[b][r] = sum_a v[8a + b] e^{-j 2 pi r a / 8}   (a < 6; real rows give
+    //             Z[b][8 - r] = conj Z[b][r], so r = 0..4 are kept),
+    //   Y[r + 8q] = sum_b e^{-j 2 pi (r + 8q) b / 64} Z[b][r].
+    // Step A: item (b, row) (lanes: consecutive rows) stores Z[b][0], Z[b][4]
+    // and Z[b][1..3] as eight planes zs[8b + slot][row].
+    float *zs = reinterpret_cast<float *>(smem + kZsOff);
+    for (int it = tid; it < 8 * kYRows; it += kThreads) {
+        const int bb = it / kYRows, row = it - bb * kYRows;
+        const float *src = (row < kArea ? xt + row * kTileStride : wt + (row - kArea) * kTileStride);
+        float v[6];
 #pragma unroll
-        for (int j = 0; j < kCols; ++j) re[j] = im[j] = 0.f;
-        for (int n = 0; n < kArea; ++n) {
-            const float v = row[n];
+        for (int a = 0; a < 6; ++a) v[a] = src[8 * a + bb];
+        float *dst = zs + 8 * bb * kYRows + row;
+        dst[0] = ((v[0] + v[1]) + (v[2] + v[3])) + (v[4] + v[5]);
+        dst[kYRows] = ((v[0] - v[1]) + (v[2] - v[3])) + (v[4] - v[5]);
 #pragma unroll
-            for (int j = 0; j < kCols; ++j) {
-                const int kn = kn0 + 2 * j;
-                if (kn < kHalfCols) {
-                    const float2 cs = tw[(kn * n) & (kDft - 1)];
-                    re[j] = fmaf(v, cs.x, re[j]);
-                    im[j] = fmaf(-v, cs.y, im[j]);
-                }
+        for (int r = 1; r <= 3; ++r) {
+            float zr = 0.f, zi = 0.f;
+#pragma unroll
+            for (int a = 0; a < 6; ++a) {
+                const float2 cs = tw[(8 * r * a) & (kDft - 1)];
+                zr = fmaf(v[a], cs.x, zr);
+                zi = fmaf(-v[a], cs.y, zi);
+            }
+            dst[2 * r * kYRows] = zr;
+            dst[(2 * r + 1) * kYRows] = zi;
+        }
+    }
+    __syncthreads();
+    // Step B: item (r, row) (lanes: consecutive rows, r warp-uniform) sums
+    // Y[r + 8q] for every q with r + 8q <= 32.
+    for (int it = tid; it < 8 * kYRows; it += kThreads) {
+        const int r = it / kYRows, row = it - r * kYRows;
+        const int rr = r <= 4 ? r : 8 - r;  // conj(Z[b][8 - r]) for r > 4
+        const float sgn = r <= 4 ? 1.f : -1.f;
+        float yr[5], yi[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) yr[q] = yi[q] = 0.f;
+#pragma unroll
+        for (int bb = 0; bb < 8; ++bb) {
+            const float *z = zs + 8 * bb * kYRows + row;
+            float zr, zi;
+            if (rr == 0) {
+                zr = z[0];
+                zi = 0.f;
+            } else if (rr == 4) {
+                zr = z[kYRows];
+                zi = 0.f;
+            } else {
+                zr = z[2 * rr * kYRows];
+                zi = sgn * z[(2 * rr + 1) * kYRows];
+            }
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                if (r + 8 * q > kDft / 2) break;
+                // (c - j s)(zr + j zi)
+                const float2 cs = tw[((r + 8 * q) * bb) & (kDft - 1)];
+                yr[q] = fmaf(cs.x, zr, fmaf(cs.y, zi, yr[q]));
+                yi[q] = fmaf(cs.x, zi, fmaf(-cs.y, zr, yi[q]));
             }
         }
-        float2 *y = (which ? yw : yx) + m * kHalfCols;
+        float2 *y = (row < kArea ? yx + row * kHalfCols : yw + (row - kArea) * kHalfCols);
 #pragma unroll
-        for (int j = 0; j < kCols; ++j) {
-            const int kn = kn0 + 2 * j;
-            if (kn < kHalfCols) y[kn] = make_float2(re[j], im[j]);
-        }
+        for (int q = 0; q < 5; ++q)
+            if (r + 8 * q <= kDft / 2) y[r + 8 * q] = make_float2(yr[q], yi[q]);
     }
     __syncthreads();
 
