@@ -163,6 +163,14 @@ int fse_plan_claims(int n_frames, const int32_t *bw, const int32_t *bh,
                     const int32_t *group_of_block, int block, int workers, int mode,
                     int32_t *items, int32_t *level_start, int32_t *n_levels);
 
+/* Measured ceilings of the units the iteration loop runs on (no counterpart
+ * in the paper; used as roofline denominators): *smem_gbs = shared-memory
+ * load bandwidth of 16-byte conflict-free loads on every SM (GB/s),
+ * *fp32_tflops = packed FP32 FMA throughput on every SM (TFLOP/s).  Runs two
+ * short kernels (a few ms) on `device`, which becomes the current device.
+ * Errors: FSE_EINVAL (NULL output, bad device), FSE_ENOMEM, FSE_ECUDA. */
+int fse_measure_peaks(int device, double *smem_gbs, double *fp32_tflops);
+
 /* Create a context on CUDA device `device`.  mem_budget bounds the device
  * workspace the context may hold (0 = no limit).  The context owns its
  * workspace (FP32 working frames, plans, status words) and a serving

@@ -24,7 +24,7 @@ FSE_MAX_ITERS = 1024
 EXPORTED = [
     "fse_plan_order", "fse_plan_claims", "fse_ctx_create", "fse_ctx_destroy", "fse_conceal_batch",
     "fse_conceal_batch_host", "fse_extrapolate_areas", "fse_submit", "fse_poll",
-    "fse_drain", "fse_last_batch_info", "fse_ctx_set_option", "fse_copy_work", "fse_copy_trace", "fse_last_kernel_ms", "fse_conceal_frame_noalloc", "fse_strerror",
+    "fse_drain", "fse_last_batch_info", "fse_ctx_set_option", "fse_copy_work", "fse_copy_trace", "fse_last_kernel_ms", "fse_conceal_frame_noalloc", "fse_measure_peaks", "fse_strerror",
 ]
 FSE_OPT_SPIN_LIMIT, FSE_OPT_PERSISTENT_CTAS, FSE_OPT_SERVE_SLOTS = 1, 2, 3
 FSE_OPT_SERVE_MAX_BATCH, FSE_OPT_TEST_STUCK_DEP, FSE_OPT_KEEP_TRACE = 4, 5, 6
@@ -71,6 +71,8 @@ def lib() -> ctypes.CDLL:
     vp, i32, cint = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int
     L.fse_plan_order.argtypes = [cint, cint, vp, cint, vp, vp, vp, ctypes.POINTER(i32)]
     L.fse_plan_claims.argtypes = [cint, vp, vp, vp, cint, cint, cint, vp, vp, ctypes.POINTER(i32)]
+    L.fse_measure_peaks.argtypes = [cint, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double)]
     L.fse_ctx_create.argtypes = [ctypes.POINTER(vp), cint, ctypes.c_size_t]
     L.fse_ctx_destroy.argtypes = [vp]
     L.fse_ctx_destroy.restype = None
@@ -132,6 +134,15 @@ def fse_plan_order(block_lost: np.ndarray, order: int):
            "fse_plan_order")
     n = ng.value
     return gob.reshape(bh, bw), gptr[:n + 1].copy(), ids[:int(gptr[n])].copy()
+
+
+def fse_measure_peaks(device: int = 0):
+    """Measured shared-memory load bandwidth (GB/s) and packed FP32 FMA
+    throughput (TFLOP/s) of the device."""
+    smem, fp32 = ctypes.c_double(0), ctypes.c_double(0)
+    _check(lib().fse_measure_peaks(int(device), ctypes.byref(smem), ctypes.byref(fp32)),
+           "fse_measure_peaks")
+    return smem.value, fp32.value
 
 
 def fse_plan_claims(group_maps, block: int = 16, workers: int = 0, mode: int = 0):
