@@ -200,6 +200,24 @@ def test_host_entry_point_matches_device(fse, ctx):
     assert np.array_equal(out, dev_out)
 
 
+@pytest.mark.parametrize("h,w", [(37, 53), (100, 130), (64, 200)])
+@pytest.mark.parametrize("executor", EXECS)
+def test_host_entry_odd_sizes_pixel_losses(fse, ctx, h, w, executor):
+    """Widths that are not a multiple of 16: device frames with such a row
+    pitch are gathered with plain loads, while the host-frame path pads the
+    device rows to 16 bytes and stages the areas with TMA; its block-loss maps
+    come from the host masks.  Both must give the same bytes."""
+    img = fse_synth.make_image(h, w, 500 + h + w)
+    rng = np.random.default_rng(h * w)
+    mask = (rng.random(img.shape) < 0.05).astype(np.uint8)
+    mask[h // 4:h // 4 + 20, w // 3:w // 3 + 25] = 1
+    p = _params(fse, 60, 1, executor)
+    (dev_out,), _ = gpu_conceal(ctx, [(img, mask)], p, want_work=False)
+    out = np.empty_like(img)
+    ctx.fse_conceal_batch_host([(img, mask, out)], p)
+    assert np.array_equal(out, dev_out)
+
+
 def test_full_size_batch_sampled_frames(fse, ctx):
     """16 x 1920x1080, K = 200, one persistent launch (the benchmark's
     configuration); frames 0 and 5 are recomputed by the oracle in full."""
