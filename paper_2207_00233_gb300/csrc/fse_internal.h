@@ -154,8 +154,6 @@ struct WorkQueue {
 cudaError_t launch_block_loss(const FrameDesc *frames_dev, int n_frames,
                               int max_blocks, uint8_t *lost_out,
                               const int *lost_off_dev, cudaStream_t stream);
-cudaError_t launch_init_frames(const FrameDesc *frames_dev, int n_frames,
-                               int max_pixels, cudaStream_t stream);
 cudaError_t launch_group(const FrameDesc *frames_dev, const int2 *items,
                          int n_items, const KParams &kp, const float *rho_tab,
                          const float2 *tw_tab, int precision,

@@ -1328,10 +1328,6 @@ cudaError_t launch_block_loss(const FrameDesc *frames_dev, int n_frames, int max
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_frames(const FrameDesc *, int, int, cudaStream_t) {
-    return cudaSuccess;
-}
-
 cudaError_t launch_group(const FrameDesc *frames_dev, const int2 *items, int n_items,
                          const KParams &kp, const float *rho_tab, const float2 *tw_tab,
                          int precision, cudaStream_t stream) {
