@@ -3,8 +3,10 @@
 // processing-order groups (Sec. 3, Algorithm 1).
 //
 // One CTA of 256 threads extrapolates one lost 16x16 block:
-//   gather   48x48 area from the frame, sub-area classes, Eq. (2) weights
-//   project  R_w = DFT64(w*f), W = DFT64(w)  (separable; real input)
+//   gather   48x48 area from the frame (luma and mask tiles by TMA bulk
+//            tensor copies), sub-area classes, Eq. (2) weights
+//   project  R_w = DFT64(w*f), W = DFT64(w)  (separable, real input; FP32
+//            8-point split DFTs, or DFT-as-GEMM on the tensor cores)
 //   iterate  K x { u = argmax |R_w|^2 ; dc = gamma R_w[u] / W[0] ;
 //                  R_w[k] -= dc W[k - u] }       (Sec. 4, transform domain)
 //   insert   Re sum dc_i phi_{u_i} on the lost samples of the block (Eq. (1))
