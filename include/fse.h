@@ -73,7 +73,8 @@ extern "C" {
 
 /* How the groups are dispatched on the device. */
 #define FSE_EXEC_GROUPS 0      /* one launch per dependency level (blocks of a
-                                  level are independent; plain path)           */
+                                  level are independent), or per group with
+                                  FSE_OPT_GROUP_LAUNCHES (the plain path)      */
 #define FSE_EXEC_PERSISTENT 1  /* one persistent launch over all frames; a block
                                   starts once every earlier-group block whose
                                   samples lie in its area has published its
@@ -302,6 +303,9 @@ int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_params *params,
  *                            persistent batch, so its bounded wait runs out
  *   FSE_OPT_KEEP_TRACE       1 records the selection trace of every block
  *                            (see fse_copy_trace); 0 (default) does not
+ *   FSE_OPT_GROUP_LAUNCHES   1: FSE_EXEC_GROUPS launches once per group of
+ *                            the processing order (Sec. 3, the plain path),
+ *                            0 (default): once per dependency level
  * Errors: FSE_EINVAL for an unknown option or value. */
 #define FSE_OPT_SPIN_LIMIT 1
 #define FSE_OPT_PERSISTENT_CTAS 2
@@ -309,6 +313,7 @@ int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_params *params,
 #define FSE_OPT_SERVE_MAX_BATCH 4
 #define FSE_OPT_TEST_STUCK_DEP 5
 #define FSE_OPT_KEEP_TRACE 6
+#define FSE_OPT_GROUP_LAUNCHES 7
 int fse_ctx_set_option(fse_ctx *ctx, int option, long long value);
 
 const char *fse_strerror(int status);

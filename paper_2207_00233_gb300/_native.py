@@ -28,6 +28,7 @@ EXPORTED = [
 ]
 FSE_OPT_SPIN_LIMIT, FSE_OPT_PERSISTENT_CTAS, FSE_OPT_SERVE_SLOTS = 1, 2, 3
 FSE_OPT_SERVE_MAX_BATCH, FSE_OPT_TEST_STUCK_DEP, FSE_OPT_KEEP_TRACE = 4, 5, 6
+FSE_OPT_GROUP_LAUNCHES = 7
 
 
 class fse_params(ctypes.Structure):

@@ -527,11 +527,24 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
     }
     std::vector<int2> items;
     std::vector<int> level_start;
-    if (persistent)
+    if (persistent) {
         delay_claims(depths, std::max(grid, 1), items,
                      [&](int n, const std::function<void(int)> &fn) { ctx->pool.run(n, fn); });
-    else
+    } else if (ctx->group_launches) {
+        // one launch per plan group: group g of every frame, frame by frame
+        items.reserve(lost_blocks);
+        level_start.assign(1, 0);
+        for (int g = 0; g < max_groups; ++g) {
+            for (int i = 0; i < n; ++i) {
+                const auto &gp = frame_gptr[i];
+                if (g + 1 >= (int)gp.size()) continue;
+                for (int j = gp[g]; j < gp[g + 1]; ++j) items.push_back(make_int2(i, frame_ids[i][j]));
+            }
+            level_start.push_back((int)items.size());
+        }
+    } else {
         level_claims(depths, items, level_start);
+    }
     const int n_launch_levels = persistent ? 0 : (int)level_start.size() - 1;
 
     // ---- uploads ----
@@ -908,6 +921,10 @@ extern "C" int fse_ctx_set_option(fse_ctx *ctx, int option, long long value) {
     case FSE_OPT_TEST_STUCK_DEP:
         if (value != 0 && value != 1) return FSE_EINVAL;
         ctx->test_stuck_dep = value != 0;
+        return FSE_OK;
+    case FSE_OPT_GROUP_LAUNCHES:
+        if (value != 0 && value != 1) return FSE_EINVAL;
+        ctx->group_launches = value != 0;
         return FSE_OK;
     default:
         return FSE_EINVAL;

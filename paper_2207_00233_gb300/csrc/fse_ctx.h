@@ -106,6 +106,7 @@ struct fse_ctx {
     int persistent_ctas = 0;   // per SM; 0 = occupancy limit
     bool test_stuck_dep = false;
     bool keep_trace = false;
+    bool group_launches = false;  // groups executor: one launch per plan group
 
     fse::DevBuf tw_dev;                                   // 64 twiddles
     std::vector<std::pair<float, fse::DevBuf>> rho_tabs;  // Eq. (2) decay per (rho, block)

@@ -118,14 +118,22 @@ def test_mixed_512_paper_rho(fse, ctx):
 
 
 def test_executors_bit_identical(fse, ctx):
+    """Launch per dependency level, launch per plan group, and the persistent
+    launch read the same samples in every block: identical bytes."""
     img, mask = fse_synth.workload_mixed_512()[0]
     res = []
-    for ex in EXECS:
+    for ex, per_group in (("groups", 0), ("groups", 1), ("persistent", 0)):
+        ctx.fse_ctx_set_option(fse.FSE_OPT_GROUP_LAUNCHES, per_group)
         p = _params(fse, 200, fse.FSE_ORDER_OPTIMIZED, ex)
         outs, works = gpu_conceal(ctx, [(img, mask)], p)
-        res.append((outs[0], works[0]))
-    assert np.array_equal(res[0][0], res[1][0])
-    assert np.array_equal(res[0][1], res[1][1], equal_nan=True)
+        res.append((outs[0], works[0], ctx.fse_last_batch_info()))
+    ctx.fse_ctx_set_option(fse.FSE_OPT_GROUP_LAUNCHES, 0)
+    for o, wk, _ in res[1:]:
+        assert np.array_equal(res[0][0], o)
+        assert np.array_equal(res[0][1], wk, equal_nan=True)
+    # one launch per group (plus the loss map) against fewer per level
+    assert res[1][2]["launches"] == res[1][2]["groups"] + 1
+    assert res[0][2]["launches"] < res[1][2]["launches"]
 
 
 @pytest.mark.parametrize("h,w,rate,seed", [(40, 56, 0.5, 1), (100, 70, 0.3, 2),
