@@ -239,6 +239,11 @@ int fse_drain(fse_ctx *ctx, int timeout_ms);
 int fse_last_batch_info(fse_ctx *ctx, int *lost_blocks, int *groups,
                         int *launches);
 
+/* Launch configuration the last fse_conceal_batch / _host call ran with:
+ * *executor (FSE_EXEC_*) and *ctas_per_sm (persistent CTAs per SM; 0 for
+ * FSE_EXEC_GROUPS).  Either pointer may be NULL.  Errors: FSE_EINVAL. */
+int fse_last_batch_config(fse_ctx *ctx, int *executor, int *ctas_per_sm);
+
 /* Device time of the extrapolation launches of the last fse_conceal_batch
  * or fse_conceal_batch_host call (the persistent kernel, or all group
  * launches), from CUDA events recorded on the call's stream around them.
@@ -306,6 +311,16 @@ int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_params *params,
  *   FSE_OPT_GROUP_LAUNCHES   1: FSE_EXEC_GROUPS launches once per group of
  *                            the processing order (Sec. 3, the plain path),
  *                            0 (default): once per dependency level
+ *   FSE_OPT_AUTOTUNE         1: fse_conceal_batch calls with
+ *                            FSE_EXEC_PERSISTENT choose, per batch shape
+ *                            (frames, samples, K, B, order, precision), the
+ *                            fastest of the launch configurations whose
+ *                            results are identical: the persistent launch
+ *                            with 1 .. (occupancy limit) CTAs per SM, or one
+ *                            launch per dependency level.  The first call of
+ *                            a shape runs and times every candidate (same
+ *                            output bytes); later calls reuse the choice.
+ *                            0 (default): as requested.
  * Errors: FSE_EINVAL for an unknown option or value. */
 #define FSE_OPT_SPIN_LIMIT 1
 #define FSE_OPT_PERSISTENT_CTAS 2
@@ -314,6 +329,7 @@ int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_params *params,
 #define FSE_OPT_TEST_STUCK_DEP 5
 #define FSE_OPT_KEEP_TRACE 6
 #define FSE_OPT_GROUP_LAUNCHES 7
+#define FSE_OPT_AUTOTUNE 8
 int fse_ctx_set_option(fse_ctx *ctx, int option, long long value);
 
 const char *fse_strerror(int status);

@@ -24,11 +24,11 @@ FSE_MAX_ITERS = 1024
 EXPORTED = [
     "fse_plan_order", "fse_plan_claims", "fse_ctx_create", "fse_ctx_destroy", "fse_conceal_batch",
     "fse_conceal_batch_host", "fse_extrapolate_areas", "fse_submit", "fse_poll",
-    "fse_drain", "fse_last_batch_info", "fse_ctx_set_option", "fse_copy_work", "fse_copy_trace", "fse_last_kernel_ms", "fse_conceal_frame_noalloc", "fse_measure_peaks", "fse_strerror",
+    "fse_drain", "fse_last_batch_info", "fse_last_batch_config", "fse_ctx_set_option", "fse_copy_work", "fse_copy_trace", "fse_last_kernel_ms", "fse_conceal_frame_noalloc", "fse_measure_peaks", "fse_strerror",
 ]
 FSE_OPT_SPIN_LIMIT, FSE_OPT_PERSISTENT_CTAS, FSE_OPT_SERVE_SLOTS = 1, 2, 3
 FSE_OPT_SERVE_MAX_BATCH, FSE_OPT_TEST_STUCK_DEP, FSE_OPT_KEEP_TRACE = 4, 5, 6
-FSE_OPT_GROUP_LAUNCHES = 7
+FSE_OPT_GROUP_LAUNCHES, FSE_OPT_AUTOTUNE = 7, 8
 
 
 class fse_params(ctypes.Structure):
@@ -86,6 +86,7 @@ def lib() -> ctypes.CDLL:
                              ctypes.POINTER(ctypes.c_uint64)]
     L.fse_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(cint), ctypes.POINTER(fse_stats)]
     L.fse_drain.argtypes = [vp, cint]
+    L.fse_last_batch_config.argtypes = [vp, ctypes.POINTER(cint), ctypes.POINTER(cint)]
     L.fse_last_batch_info.argtypes = [vp, ctypes.POINTER(cint), ctypes.POINTER(cint),
                                       ctypes.POINTER(cint)]
     L.fse_ctx_set_option.argtypes = [vp, cint, ctypes.c_longlong]
@@ -299,6 +300,12 @@ class Context:
     def fse_ctx_set_option(self, option: int, value: int) -> None:
         _check(lib().fse_ctx_set_option(self.handle, int(option), int(value)),
                "fse_ctx_set_option")
+
+    def fse_last_batch_config(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(lib().fse_last_batch_config(self.handle, ctypes.byref(a), ctypes.byref(b)),
+               "fse_last_batch_config")
+        return {"executor": a.value, "ctas_per_sm": b.value}
 
     def fse_last_batch_info(self):
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

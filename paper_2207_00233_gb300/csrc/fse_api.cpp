@@ -384,7 +384,7 @@ void fse::WorkerPool::run(int n, const std::function<void(int)> &fn) {
 
 int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
                    const fse_params *p, cudaStream_t stream,
-                   const std::vector<std::vector<uint8_t>> *host_lost) {
+                   const std::vector<std::vector<uint8_t>> *host_lost, int ctas_per_sm) {
     int rc = FSE_OK;
     const float *rho_tab = ctx->rho_table(p->rho, p->block, &rc);
     if (!rho_tab) return rc;
@@ -520,11 +520,15 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
     // of the persistent CTAs ----
     const bool persistent = p->executor == FSE_EXEC_PERSISTENT;
     int grid = 0;
+    int per_sm = 0;
     if (persistent) {
-        int per_sm = max_resident_ctas(p->iters);
-        if (ctx->persistent_ctas > 0) per_sm = std::min(per_sm, ctx->persistent_ctas);
+        per_sm = max_resident_ctas(p->iters);
+        const int cap = ctas_per_sm >= 0 ? ctas_per_sm : ctx->persistent_ctas;
+        if (cap > 0) per_sm = std::min(per_sm, cap);
         grid = std::min<int>(lost_blocks, ctx->num_sms * per_sm);
     }
+    ws.executor = p->executor;
+    ws.ctas_per_sm = per_sm;
     std::vector<int2> items;
     std::vector<int> level_start;
     if (persistent) {
@@ -754,6 +758,66 @@ extern "C" void fse_ctx_destroy(fse_ctx *ctx) {
     delete ctx;
 }
 
+// FSE_OPT_AUTOTUNE: the first batch of a shape runs every launch
+// configuration with identical results and keeps the fastest (device time
+// from the call's start to its last launch, planning included).
+static int autotuned_batch(fse_ctx *ctx, const fse_frame *frames, int n,
+                           const fse_params *params, cudaStream_t stream) {
+    long long samples = 0;
+    for (int i = 0; i < n; ++i) samples += (long long)frames[i].width * frames[i].height;
+    const std::vector<long long> key = {n, samples, params->iters, params->block, params->order,
+                                        params->precision};
+    fse_params p = *params;
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end()) {
+        p.executor = it->second.first;
+        return run_batch(ctx, ctx->ws, frames, n, &p, stream, nullptr, it->second.second);
+    }
+    std::vector<std::pair<int, int>> cand;
+    const int max_per_sm = max_resident_ctas(params->iters);
+    for (int c = max_per_sm; c >= 1; --c) cand.emplace_back(FSE_EXEC_PERSISTENT, c);
+    cand.emplace_back(FSE_EXEC_GROUPS, 0);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        return FSE_ECUDA;
+    }
+    float best = -1.f;
+    std::pair<int, int> choice = cand.front();
+    int rc = FSE_OK;
+    for (const auto &c : cand) {
+        p.executor = c.first;
+        if (cudaEventRecord(e0, stream) != cudaSuccess) {
+            rc = FSE_ECUDA;
+            break;
+        }
+        rc = run_batch(ctx, ctx->ws, frames, n, &p, stream, nullptr, c.second);
+        if (!rc) rc = read_status(ctx, ctx->ws, stream);
+        if (rc) break;
+        float ms = 0.f;
+        if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = FSE_ECUDA;
+            break;
+        }
+        if (best < 0.f || ms < best) {
+            best = ms;
+            choice = c;
+        }
+    }
+    if (rc) cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    ctx->tuned[key] = choice;
+    // the last candidate's output stands (every candidate gives the same
+    // bytes); report the chosen configuration
+    ctx->ws.executor = choice.first;
+    ctx->ws.ctas_per_sm = choice.second;
+    return FSE_OK;
+}
+
 extern "C" int fse_conceal_batch(fse_ctx *ctx, const fse_frame *frames, int n,
                                  const fse_params *params, void *cuda_stream) {
     if (!ctx || !frames || n <= 0) return FSE_EINVAL;
@@ -763,11 +827,16 @@ extern "C" int fse_conceal_batch(fse_ctx *ctx, const fse_frame *frames, int n,
         if ((rc = check_frame(frames[i]))) return rc;
     std::lock_guard<std::mutex> lk(ctx->api_mu);
     cudaSetDevice(ctx->device);
-    rc = run_batch(ctx, ctx->ws, frames, n, params, static_cast<cudaStream_t>(cuda_stream),
-                   nullptr);
+    if (ctx->autotune && params->executor == FSE_EXEC_PERSISTENT)
+        rc = autotuned_batch(ctx, frames, n, params, static_cast<cudaStream_t>(cuda_stream));
+    else
+        rc = run_batch(ctx, ctx->ws, frames, n, params, static_cast<cudaStream_t>(cuda_stream),
+                       nullptr);
     ctx->last_lost_blocks = ctx->ws.lost_blocks;
     ctx->last_groups = ctx->ws.groups;
     ctx->last_launches = ctx->ws.launches;
+    ctx->last_executor = ctx->ws.executor;
+    ctx->last_ctas = ctx->ws.ctas_per_sm;
     return rc;
 }
 
@@ -814,6 +883,8 @@ extern "C" int fse_conceal_batch_host(fse_ctx *ctx, const fse_frame *frames, int
     ctx->last_lost_blocks = ws.lost_blocks;
     ctx->last_groups = ws.groups;
     ctx->last_launches = ws.launches;
+    ctx->last_executor = ws.executor;
+    ctx->last_ctas = ws.ctas_per_sm;
     if (rc) return rc;
     for (int i = 0; i < n; ++i) {
         const fse_frame &h = frames[i];
@@ -850,6 +921,14 @@ extern "C" int fse_last_batch_info(fse_ctx *ctx, int *lost_blocks, int *groups, 
     if (lost_blocks) *lost_blocks = ctx->last_lost_blocks;
     if (groups) *groups = ctx->last_groups;
     if (launches) *launches = ctx->last_launches;
+    return FSE_OK;
+}
+
+extern "C" int fse_last_batch_config(fse_ctx *ctx, int *executor, int *ctas_per_sm) {
+    if (!ctx) return FSE_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    if (executor) *executor = ctx->last_executor;
+    if (ctas_per_sm) *ctas_per_sm = ctx->last_ctas;
     return FSE_OK;
 }
 
@@ -926,6 +1005,12 @@ extern "C" int fse_ctx_set_option(fse_ctx *ctx, int option, long long value) {
         if (value != 0 && value != 1) return FSE_EINVAL;
         ctx->group_launches = value != 0;
         return FSE_OK;
+    case FSE_OPT_AUTOTUNE: {
+        if (value != 0 && value != 1) return FSE_EINVAL;
+        std::lock_guard<std::mutex> lk(ctx->api_mu);
+        ctx->autotune = value != 0;
+        return FSE_OK;
+    }
     default:
         return FSE_EINVAL;
     }

@@ -5,6 +5,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <functional>
+#include <map>
 #include <cstdint>
 #include <deque>
 #include <mutex>
@@ -39,6 +40,7 @@ struct Workspace {
     bool k_timed = false;
     bool status_live = false;      // status word of the last launch pending
     int lost_blocks = 0, groups = 0, launches = 0;  // of the last batch
+    int executor = 0, ctas_per_sm = 0;              // its launch configuration
     std::vector<int16_t *> trace_ptr;               // per frame of the last batch
     std::vector<size_t> trace_len;
     std::vector<float *> work_ptr;
@@ -107,6 +109,10 @@ struct fse_ctx {
     bool test_stuck_dep = false;
     bool keep_trace = false;
     bool group_launches = false;  // groups executor: one launch per plan group
+    bool autotune = false;        // choose the launch configuration per shape
+    // autotuned (executor, CTAs per SM) per batch shape
+    std::map<std::vector<long long>, std::pair<int, int>> tuned;
+    int last_executor = 0, last_ctas = 0;  // configuration of the last batch
 
     fse::DevBuf tw_dev;                                   // 64 twiddles
     std::vector<std::pair<float, fse::DevBuf>> rho_tabs;  // Eq. (2) decay per (rho, block)
@@ -147,9 +153,11 @@ struct fse_ctx {
 namespace fse {
 // Block-loss map [bh][bw] of a frame in host memory.
 std::vector<uint8_t> host_block_loss(const fse_frame &f, int B);
+// ctas_per_sm: persistent CTAs per SM for this batch (< 0: the context's
+// FSE_OPT_PERSISTENT_CTAS setting).
 int run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
               const fse_params *p, cudaStream_t stream,
-              const std::vector<std::vector<uint8_t>> *host_lost);
+              const std::vector<std::vector<uint8_t>> *host_lost, int ctas_per_sm = -1);
 int read_status(fse_ctx *ctx, Workspace &ws, cudaStream_t stream);
 void release_workspace(fse_ctx *ctx, Workspace &ws);
 void stop_server(fse_ctx *ctx);

@@ -348,3 +348,31 @@ def test_device_wait_timeout_reports_status(fse, ctx):
     ctx.fse_conceal_batch_host([(img, mask, out)], p)
     (ref,), _ = gpu_conceal(ctx, [(img, mask)], p, want_work=False)
     assert np.array_equal(out, ref)
+
+
+def test_autotune_same_bytes_and_cached(fse, ctx):
+    """FSE_OPT_AUTOTUNE picks among launch configurations with identical
+    results: the output equals the untuned one, the first call of a shape
+    tunes, and the second reuses the choice."""
+    frames = [fse_synth.random_frame(h, w, rate, s) for (h, w, rate, s) in
+              [(96, 128, 0.3, 41), (64, 80, 0.5, 42)]]
+    p = _params(fse, 60, 1, "persistent")
+    ref_out, ref_work = gpu_conceal(ctx, frames, p)
+    ctx.fse_ctx_set_option(fse.FSE_OPT_AUTOTUNE, 1)
+    try:
+        out1, work1 = gpu_conceal(ctx, frames, p)
+        cfg1 = ctx.fse_last_batch_config()
+        out2, work2 = gpu_conceal(ctx, frames, p)
+        cfg2 = ctx.fse_last_batch_config()
+    finally:
+        ctx.fse_ctx_set_option(fse.FSE_OPT_AUTOTUNE, 0)
+    for a, b in zip(ref_out + ref_work, out1 + work1):
+        assert np.array_equal(a, b, equal_nan=True)
+    for a, b in zip(ref_out + ref_work, out2 + work2):
+        assert np.array_equal(a, b, equal_nan=True)
+    assert cfg1 == cfg2
+    if cfg1["executor"] == fse.FSE_EXEC_PERSISTENT:
+        assert 1 <= cfg1["ctas_per_sm"] <= 3
+    else:
+        assert cfg1["executor"] == fse.FSE_EXEC_GROUPS and cfg1["ctas_per_sm"] == 0
+    print(cfg1)
