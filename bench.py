@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--precision", default="fp32",
+                    choices=["fp32", "tf32", "bf16", "fp16", "bf16x3", "tf32x3"],
+                    help="projection arithmetic of the main workload (profiling the "
+                         "tensor-core path); the iterations are FP32 in every case")
     return ap.parse_args()
 
 
@@ -380,9 +384,11 @@ def main():
 
     frames = make_workload(args.frames)
     ctx = fse.Context(local)
+    prec = {"fp32": fse.FSE_PREC_FP32, "tf32": fse.FSE_PREC_TF32, "bf16": fse.FSE_PREC_BF16,
+            "fp16": fse.FSE_PREC_FP16, "bf16x3": fse.FSE_PREC_BF16X3,
+            "tf32x3": fse.FSE_PREC_TF32X3}[args.precision]
     params = fse.make_params(iters=K_ITERS, order=fse.FSE_ORDER_OPTIMIZED,
-                             executor=fse.FSE_EXEC_PERSISTENT, precision=fse.FSE_PREC_FP32,
-                             **PARAMS)
+                             executor=fse.FSE_EXEC_PERSISTENT, precision=prec, **PARAMS)
     tens = []
     for img, mask in frames:
         l = torch.from_numpy(img).to(dev)
@@ -488,7 +494,10 @@ def main():
         peak_source = "derived: 152 SMs x 128 B/clk x 2070 MHz (max SM clock)"
     achieved = smem_bytes / (k_ms / 1e3) / 1e9
     roofline = {"bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
-                "frac": achieved / smem_peak, "traffic": TRAFFIC_BYTES_PER_LAUNCH,
+                "frac": achieved / smem_peak,
+                # the capture is of the default workload (16 frames, FP32 projection)
+                "traffic": (TRAFFIC_BYTES_PER_LAUNCH
+                            if args.precision == "fp32" and args.frames == FRAMES else None),
                 "kernel": "k_persistent", "kernel_ms": k_ms,
                 "peak_source": peak_source,
                 "fp32": {"achieved_tflops": flops / (k_ms / 1e3) / 1e12, "peak_tflops": fp32_peak,
@@ -518,7 +527,7 @@ def main():
                        "executor": ("persistent" if launch_cfg["executor"] == fse.FSE_EXEC_PERSISTENT
                                     else "levels"),
                        "ctas_per_sm": launch_cfg["ctas_per_sm"], "autotuned": True,
-                       "precision": "fp32",
+                       "precision": args.precision,
                        "lost_blocks_per_step": lost_blocks,
                        "l2": "flushed between steps (256 MiB write, outside the timed events)",
                        "parallelism": f"replicas x{world}", **PARAMS},
