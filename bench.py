@@ -431,6 +431,8 @@ def main():
     t_ms = float(np.sum(step_ms))
     t_max = max_over_ranks(t_ms, dev)
     value = weak_scaling_value(lost_blocks, args.steps, t_max, world)
+    lost_pixels = int(sum(int((mask != 0).sum()) for _, mask in frames))
+    mpixel = weak_scaling_value(lost_pixels, args.steps, t_max, world) / 1e6
 
     # ---- end to end through the host-buffer entry point ----
     pinned = []
@@ -528,13 +530,14 @@ def main():
                                     else "levels"),
                        "ctas_per_sm": launch_cfg["ctas_per_sm"], "autotuned": True,
                        "precision": args.precision,
-                       "lost_blocks_per_step": lost_blocks,
+                       "lost_blocks_per_step": lost_blocks, "lost_pixels_per_step": lost_pixels,
                        "l2": "flushed between steps (256 MiB write, outside the timed events)",
                        "parallelism": f"replicas x{world}", **PARAMS},
             "e2e": {"value": lost_blocks / (e2e_ms / 1e3) * world, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_ms},
             "gpu_launches": launches_per_step * args.steps,
+            "lost_mpixel_per_s": mpixel,
             "roofline": roofline,
             "clocks": clk,
             "plain_path": None if plain is None else {
