@@ -239,6 +239,13 @@ int fse_drain(fse_ctx *ctx, int timeout_ms);
 int fse_last_batch_info(fse_ctx *ctx, int *lost_blocks, int *groups,
                         int *launches);
 
+/* Device times of the extrapolation launches of the last min(n, 64) device
+ * batches of the synchronous API that launched any (ms[0] the most recent),
+ * from the same CUDA events as fse_last_kernel_ms; *count receives how many
+ * were written.  Waits for their end events.  Lets a caller time a run of
+ * batches without synchronising between them.  Errors: FSE_EINVAL, FSE_ECUDA. */
+int fse_recent_kernel_ms(fse_ctx *ctx, int n, float *ms, int *count);
+
 /* Launch configuration the last fse_conceal_batch / _host call ran with:
  * *executor (FSE_EXEC_*) and *ctas_per_sm (persistent CTAs per SM; 0 for
  * FSE_EXEC_GROUPS).  Either pointer may be NULL.  Errors: FSE_EINVAL. */
@@ -321,6 +328,15 @@ int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_params *params,
  *                            a shape runs and times every candidate (same
  *                            output bytes); later calls reuse the choice.
  *                            0 (default): as requested.
+ *   FSE_OPT_INPUTS_READY     1: the loss masks of each fse_conceal_batch call
+ *                            are complete when the call is made (no work
+ *                            still queued on its stream writes them); the
+ *                            call copies them to the host on a side stream
+ *                            and plans the batch while the stream's earlier
+ *                            work (a previous batch) still runs.  A failed
+ *                            device wait of a batch is then reported by a
+ *                            later call.  0 (default): the masks are read in
+ *                            stream order.
  * Errors: FSE_EINVAL for an unknown option or value. */
 #define FSE_OPT_SPIN_LIMIT 1
 #define FSE_OPT_PERSISTENT_CTAS 2
@@ -330,6 +346,7 @@ int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_params *params,
 #define FSE_OPT_KEEP_TRACE 6
 #define FSE_OPT_GROUP_LAUNCHES 7
 #define FSE_OPT_AUTOTUNE 8
+#define FSE_OPT_INPUTS_READY 9
 int fse_ctx_set_option(fse_ctx *ctx, int option, long long value);
 
 const char *fse_strerror(int status);

@@ -24,11 +24,11 @@ FSE_MAX_ITERS = 1024
 EXPORTED = [
     "fse_plan_order", "fse_plan_claims", "fse_ctx_create", "fse_ctx_destroy", "fse_conceal_batch",
     "fse_conceal_batch_host", "fse_extrapolate_areas", "fse_submit", "fse_poll",
-    "fse_drain", "fse_last_batch_info", "fse_last_batch_config", "fse_ctx_set_option", "fse_copy_work", "fse_copy_trace", "fse_last_kernel_ms", "fse_conceal_frame_noalloc", "fse_measure_peaks", "fse_strerror",
+    "fse_drain", "fse_last_batch_info", "fse_last_batch_config", "fse_ctx_set_option", "fse_copy_work", "fse_copy_trace", "fse_last_kernel_ms", "fse_recent_kernel_ms", "fse_conceal_frame_noalloc", "fse_measure_peaks", "fse_strerror",
 ]
 FSE_OPT_SPIN_LIMIT, FSE_OPT_PERSISTENT_CTAS, FSE_OPT_SERVE_SLOTS = 1, 2, 3
 FSE_OPT_SERVE_MAX_BATCH, FSE_OPT_TEST_STUCK_DEP, FSE_OPT_KEEP_TRACE = 4, 5, 6
-FSE_OPT_GROUP_LAUNCHES, FSE_OPT_AUTOTUNE = 7, 8
+FSE_OPT_GROUP_LAUNCHES, FSE_OPT_AUTOTUNE, FSE_OPT_INPUTS_READY = 7, 8, 9
 
 
 class fse_params(ctypes.Structure):
@@ -87,6 +87,7 @@ def lib() -> ctypes.CDLL:
     L.fse_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(cint), ctypes.POINTER(fse_stats)]
     L.fse_drain.argtypes = [vp, cint]
     L.fse_last_batch_config.argtypes = [vp, ctypes.POINTER(cint), ctypes.POINTER(cint)]
+    L.fse_recent_kernel_ms.argtypes = [vp, cint, vp, ctypes.POINTER(cint)]
     L.fse_last_batch_info.argtypes = [vp, ctypes.POINTER(cint), ctypes.POINTER(cint),
                                       ctypes.POINTER(cint)]
     L.fse_ctx_set_option.argtypes = [vp, cint, ctypes.c_longlong]
@@ -300,6 +301,14 @@ class Context:
     def fse_ctx_set_option(self, option: int, value: int) -> None:
         _check(lib().fse_ctx_set_option(self.handle, int(option), int(value)),
                "fse_ctx_set_option")
+
+    def fse_recent_kernel_ms(self, n: int):
+        """Kernel times (ms) of the last n batches, most recent first."""
+        buf = (ctypes.c_float * max(n, 1))()
+        cnt = ctypes.c_int(0)
+        _check(lib().fse_recent_kernel_ms(self.handle, int(n), buf, ctypes.byref(cnt)),
+               "fse_recent_kernel_ms")
+        return [buf[j] for j in range(cnt.value)]
 
     def fse_last_batch_config(self):
         a, b = ctypes.c_int(), ctypes.c_int()

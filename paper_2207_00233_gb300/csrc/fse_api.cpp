@@ -382,6 +382,27 @@ void fse::WorkerPool::run(int n, const std::function<void(int)> &fn) {
     fn_ = nullptr;
 }
 
+// FSE_OPT_INPUTS_READY: statuses of earlier batches whose read-back has
+// completed; FSE_ETIMEDOUT if one of them reported a failed device wait.
+// `wait_slot` >= 0 also waits for that slot (before it is reused).
+static int poll_status_ring(Workspace &ws, int wait_slot) {
+    int rc = FSE_OK;
+    for (int k = 0; k < 2; ++k) {
+        if (!ws.st_pending[k]) continue;
+        cudaError_t e = k == wait_slot ? cudaEventSynchronize(ws.st_ev[k])
+                                       : cudaEventQuery(ws.st_ev[k]);
+        if (e == cudaErrorNotReady) continue;
+        ws.st_pending[k] = false;
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = FSE_ECUDA;
+        } else if (static_cast<int *>(ws.st_host.ptr)[k] != 0 && rc == FSE_OK) {
+            rc = FSE_ETIMEDOUT;
+        }
+    }
+    return rc;
+}
+
 int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
                    const fse_params *p, cudaStream_t stream,
                    const std::vector<std::vector<uint8_t>> *host_lost, int ctas_per_sm) {
@@ -450,6 +471,28 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
         for (int i = 0; i < n; ++i)
             std::memcpy(lost_h.data() + lost_off[i], (*host_lost)[i].data(),
                         (size_t)fd[i].bh * fd[i].bw);
+    } else if (ctx->inputs_ready) {
+        // The masks are complete now: copy them to the host on a side stream,
+        // not behind the work queued on `stream` (typically the previous
+        // batch, still running), and build the maps there, so that planning
+        // overlaps that work.
+        if ((rc = poll_status_ring(ws, -1))) return rc;
+        if (!ws.side) CK(cudaStreamCreateWithFlags(&ws.side, cudaStreamNonBlocking));
+        size_t total = 0;
+        std::vector<size_t> moff(n + 1, 0);
+        for (int i = 0; i < n; ++i) moff[i + 1] = moff[i] + (size_t)fd[i].W * fd[i].H;
+        total = moff[n];
+        if ((rc = ctx->host_reserve(ws.mstage, std::max<size_t>(total, 1)))) return rc;
+        uint8_t *ms = static_cast<uint8_t *>(ws.mstage.ptr);
+        for (int i = 0; i < n; ++i)
+            CK(cudaMemcpy2DAsync(ms + moff[i], fd[i].W, fd[i].mask, fd[i].stride, fd[i].W,
+                                 fd[i].H, cudaMemcpyDeviceToHost, ws.side));
+        CK(cudaStreamSynchronize(ws.side));
+        ctx->pool.run(n, [&](int i) {
+            const fse_frame h{nullptr, nullptr, ms + moff[i], fd[i].W, fd[i].H, fd[i].W};
+            const std::vector<uint8_t> m = host_block_loss(h, p->block);
+            std::memcpy(lost_h.data() + lost_off[i], m.data(), m.size());
+        });
     } else {
         rc = ctx->host_reserve(ws.stage, sizeof(FrameDesc) * n + sizeof(int) * (n + 1) +
                                              nblocks + 64);
@@ -618,12 +661,13 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
     int launches = 1;  // block-loss map
     ws.k_timed = false;
     if (n_items > 0) {
-        if (!ws.k_begin) {
-            CK(cudaEventCreate(&ws.k_begin));
-            CK(cudaEventCreate(&ws.k_end));
+        const int kslot = ws.k_pos;
+        if (!ws.k_begin[kslot]) {
+            CK(cudaEventCreate(&ws.k_begin[kslot]));
+            CK(cudaEventCreate(&ws.k_end[kslot]));
         }
         CK(cudaMemsetAsync(status, 0, sizeof(int) * 2, stream));
-        CK(cudaEventRecord(ws.k_begin, stream));
+        CK(cudaEventRecord(ws.k_begin[kslot], stream));
         if (persistent) {
             WorkQueue wq;
             wq.items = static_cast<const int2 *>(ws.items.ptr);
@@ -643,9 +687,26 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
                 launches += 1;
             }
         }
-        CK(cudaEventRecord(ws.k_end, stream));
+        CK(cudaEventRecord(ws.k_end[kslot], stream));
         ws.k_timed = true;
+        ws.k_pos = (kslot + 1) % Workspace::kKernelRing;
+        ws.k_count = std::min(ws.k_count + 1, Workspace::kKernelRing);
         ws.status_live = true;
+        if (ctx->inputs_ready && !host_lost) {
+            // read the status back in stream order; a later call reports it
+            if (!ws.st_host.ptr && (rc = ctx->host_reserve(ws.st_host, 2 * sizeof(int))))
+                return rc;
+            const int slot = ws.st_slot;
+            if ((rc = poll_status_ring(ws, slot))) return rc;
+            if (!ws.st_ev[slot])
+                CK(cudaEventCreateWithFlags(&ws.st_ev[slot], cudaEventDisableTiming));
+            CK(cudaMemcpyAsync(static_cast<int *>(ws.st_host.ptr) + slot, status + 1, sizeof(int),
+                               cudaMemcpyDeviceToHost, stream));
+            CK(cudaEventRecord(ws.st_ev[slot], stream));
+            ws.st_pending[slot] = true;
+            ws.st_slot = slot ^ 1;
+            ws.status_live = false;
+        }
     }
     ws.lost_blocks = lost_blocks;
     ws.groups = max_groups;
@@ -698,10 +759,23 @@ void fse::release_workspace(fse_ctx *ctx, Workspace &ws) {
     ctx->dev_release(ws.d_mask);
     ctx->dev_release(ws.d_out);
     ctx->host_release(ws.stage);
+    ctx->host_release(ws.mstage);
+    ctx->host_release(ws.st_host);
+    for (int k = 0; k < 2; ++k) {
+        if (ws.st_ev[k]) cudaEventDestroy(ws.st_ev[k]);
+        ws.st_ev[k] = nullptr;
+        ws.st_pending[k] = false;
+    }
+    if (ws.side) cudaStreamDestroy(ws.side);
+    ws.side = nullptr;
     if (ws.staged) cudaEventDestroy(ws.staged);
-    if (ws.k_begin) cudaEventDestroy(ws.k_begin);
-    if (ws.k_end) cudaEventDestroy(ws.k_end);
-    ws.staged = ws.k_begin = ws.k_end = nullptr;
+    for (int k = 0; k < Workspace::kKernelRing; ++k) {
+        if (ws.k_begin[k]) cudaEventDestroy(ws.k_begin[k]);
+        if (ws.k_end[k]) cudaEventDestroy(ws.k_end[k]);
+        ws.k_begin[k] = ws.k_end[k] = nullptr;
+    }
+    ws.staged = nullptr;
+    ws.k_pos = ws.k_count = 0;
     ws.k_timed = false;
 }
 
@@ -938,8 +1012,25 @@ extern "C" int fse_last_kernel_ms(fse_ctx *ctx, float *ms) {
     *ms = 0.f;
     if (!ctx->ws.k_timed) return FSE_OK;
     cudaSetDevice(ctx->device);
-    CK(cudaEventSynchronize(ctx->ws.k_end));
-    CK(cudaEventElapsedTime(ms, ctx->ws.k_begin, ctx->ws.k_end));
+    const Workspace &ws = ctx->ws;
+    const int k = (ws.k_pos + Workspace::kKernelRing - 1) % Workspace::kKernelRing;
+    CK(cudaEventSynchronize(ws.k_end[k]));
+    CK(cudaEventElapsedTime(ms, ws.k_begin[k], ws.k_end[k]));
+    return FSE_OK;
+}
+
+extern "C" int fse_recent_kernel_ms(fse_ctx *ctx, int n, float *ms, int *count) {
+    if (!ctx || !ms || !count || n < 0) return FSE_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    cudaSetDevice(ctx->device);
+    const Workspace &ws = ctx->ws;
+    const int m = std::min(n, ws.k_count);
+    for (int j = 0; j < m; ++j) {  // j = 0: the most recent batch
+        const int k = (ws.k_pos + Workspace::kKernelRing - 1 - j) % Workspace::kKernelRing;
+        CK(cudaEventSynchronize(ws.k_end[k]));
+        CK(cudaEventElapsedTime(&ms[j], ws.k_begin[k], ws.k_end[k]));
+    }
+    *count = m;
     return FSE_OK;
 }
 
@@ -1005,6 +1096,12 @@ extern "C" int fse_ctx_set_option(fse_ctx *ctx, int option, long long value) {
         if (value != 0 && value != 1) return FSE_EINVAL;
         ctx->group_launches = value != 0;
         return FSE_OK;
+    case FSE_OPT_INPUTS_READY: {
+        if (value != 0 && value != 1) return FSE_EINVAL;
+        std::lock_guard<std::mutex> lk(ctx->api_mu);
+        ctx->inputs_ready = value != 0;
+        return FSE_OK;
+    }
     case FSE_OPT_AUTOTUNE: {
         if (value != 0 && value != 1) return FSE_EINVAL;
         std::lock_guard<std::mutex> lk(ctx->api_mu);

@@ -36,8 +36,12 @@ struct Workspace {
     HostBuf stage;                 // pinned staging for uploads / readback
     HostBuf io;                    // pinned staging of serving frames
     cudaEvent_t staged = nullptr;  // uploads from `stage` are complete
-    cudaEvent_t k_begin = nullptr, k_end = nullptr;  // around the extrapolation
-    bool k_timed = false;
+    // events around the extrapolation launches of the last kKernelRing
+    // batches (ring; k_pos is the next slot, k_count the recorded batches)
+    static constexpr int kKernelRing = 64;
+    cudaEvent_t k_begin[kKernelRing] = {}, k_end[kKernelRing] = {};
+    int k_pos = 0, k_count = 0;
+    bool k_timed = false;  // the last batch recorded a pair
     bool status_live = false;      // status word of the last launch pending
     int lost_blocks = 0, groups = 0, launches = 0;  // of the last batch
     int executor = 0, ctas_per_sm = 0;              // its launch configuration
@@ -45,6 +49,14 @@ struct Workspace {
     std::vector<size_t> trace_len;
     std::vector<float *> work_ptr;
     std::vector<int> work_w, work_h, work_stride;
+    // FSE_OPT_INPUTS_READY: masks copied to the host on a side stream, and the
+    // status words of batches still in flight read back in a ring of two
+    cudaStream_t side = nullptr;
+    HostBuf mstage;                 // pinned copies of the device masks
+    HostBuf st_host;                // pinned status words (2)
+    cudaEvent_t st_ev[2] = {nullptr, nullptr};
+    bool st_pending[2] = {false, false};
+    int st_slot = 0;
 };
 
 using Clock = std::chrono::steady_clock;
@@ -110,6 +122,7 @@ struct fse_ctx {
     bool keep_trace = false;
     bool group_launches = false;  // groups executor: one launch per plan group
     bool autotune = false;        // choose the launch configuration per shape
+    bool inputs_ready = false;    // masks complete at the call (plan ahead)
     // autotuned (executor, CTAs per SM) per batch shape
     std::map<std::vector<long long>, std::pair<int, int>> tuned;
     int last_executor = 0, last_ctas = 0;  // configuration of the last batch

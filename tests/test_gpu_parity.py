@@ -376,3 +376,43 @@ def test_autotune_same_bytes_and_cached(fse, ctx):
     else:
         assert cfg1["executor"] == fse.FSE_EXEC_GROUPS and cfg1["ctas_per_sm"] == 0
     print(cfg1)
+
+
+def test_inputs_ready_pipelined_planning(fse, ctx):
+    """FSE_OPT_INPUTS_READY: masks copied to the host on a side stream and
+    batches planned while the previous one runs.  Back-to-back calls on
+    different frames give the bytes of the default mode; a failed device
+    wait is reported by a later call."""
+    import torch
+    dev = torch.device("cuda:0")
+    sets = [[fse_synth.random_frame(h, w, rate, s)] for (h, w, rate, s) in
+            [(96, 160, 0.3, 51), (128, 96, 0.45, 52), (64, 64, 0.6, 53)]]
+    p = _params(fse, 60, 1, "persistent")
+    ref = [gpu_conceal(ctx, fr, p, want_work=False)[0][0] for fr in sets]
+    tens = [[(torch.from_numpy(i).to(dev), torch.from_numpy(m).to(dev),
+              torch.empty_like(torch.from_numpy(i)).to(dev)) for i, m in fr] for fr in sets]
+    ctx.fse_ctx_set_option(fse.FSE_OPT_INPUTS_READY, 1)
+    try:
+        for t in tens:  # no synchronisation between the calls
+            ctx.fse_conceal_batch(t, p)
+        torch.cuda.synchronize()
+        for t, r in zip(tens, ref):
+            assert np.array_equal(t[0][2].cpu().numpy(), r)
+        ks = ctx.fse_recent_kernel_ms(3)
+        assert len(ks) == 3 and all(k > 0 for k in ks)
+        assert ks[0] == pytest.approx(ctx.fse_last_kernel_ms())
+        # a dependency that nothing releases: the error surfaces later
+        ctx.fse_ctx_set_option(fse.FSE_OPT_SPIN_LIMIT, 2000)
+        ctx.fse_ctx_set_option(fse.FSE_OPT_TEST_STUCK_DEP, 1)
+        ctx.fse_conceal_batch(tens[0], p)
+        torch.cuda.synchronize()
+        with pytest.raises(fse.FseError) as e:
+            ctx.fse_conceal_batch(tens[1], p)
+        assert e.value.code == 4
+        ctx.fse_ctx_set_option(fse.FSE_OPT_SPIN_LIMIT, 1 << 23)
+        ctx.fse_conceal_batch(tens[2], p)
+        torch.cuda.synchronize()
+        assert np.array_equal(tens[2][0][2].cpu().numpy(), ref[2])
+    finally:
+        ctx.fse_ctx_set_option(fse.FSE_OPT_INPUTS_READY, 0)
+        ctx.fse_ctx_set_option(fse.FSE_OPT_SPIN_LIMIT, 1 << 23)
