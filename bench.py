@@ -45,7 +45,7 @@ FP32_LANES = 128
 # DRAM bytes (read + write) of one k_persistent<FP32> launch on this workload,
 # from the ncu capture summarised in profiles/k_persistent_batch16_1080p_K200.md;
 # None while the kernel differs from the captured one
-TRAFFIC_BYTES_PER_LAUNCH = 192.814592e6 + 53.346304e6
+TRAFFIC_BYTES_PER_LAUNCH = None
 
 
 def parse():

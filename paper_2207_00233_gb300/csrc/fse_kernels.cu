@@ -76,6 +76,9 @@ __device__ __forceinline__ void lds_pair(uint32_t addr, u64 &a, u64 &b) {
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
+__device__ __forceinline__ void st_shared_pair(uint32_t addr, u64 a, u64 b) {
+    asm volatile("st.shared.v2.b64 [%0], {%1, %2};" ::"r"(addr), "l"(a), "l"(b) : "memory");
+}
 
 // ---- TMA: bulk tensor copies completed on a shared-memory mbarrier ----------
 
@@ -997,20 +1000,19 @@ __device__ __forceinline__ float run_block(const Src &src, const KParams &kp,
     u64 s2 = 0ull, c2 = 0ull;
     for (int c0 = 0; c0 < K; c0 += kSynChunk) {
         const int nc = min(kSynChunk, K - c0);
-        for (int e = tid; e < nc * 32; e += kThreads) {
-            const int it = e >> 5, q = e & 31;
+        // thread (it, q) builds P[it][q] and E[it][q]: no divergent halves,
+        // and two independent table lookups per entry
+#pragma unroll 2
+        for (int e = tid; e < nc * 16; e += kThreads) {
+            const int it = e >> 4, q = e & 15;
             const int u = ul[c0 + it];
-            if (q < 16) {
-                const float2 d = dcl[c0 + it];
-                const float2 cs = tw[((u >> 6) * (kBorder + q)) & (kDft - 1)];
-                const float pr = fmaf(d.x, cs.x, -d.y * cs.y), pim = fmaf(d.x, cs.y, d.y * cs.x);
-                ptab[(it * 16 + q) * 2] = pack2(pr, pr);
-                ptab[(it * 16 + q) * 2 + 1] = pack2(-pim, -pim);
-            } else {
-                const float2 ev = tw[((u & 63) * (kBorder + q - 16)) & (kDft - 1)];
-                etab[it * 32 + (q - 16)] = ev.x;
-                etab[it * 32 + q] = ev.y;
-            }
+            const float2 d = dcl[c0 + it];
+            const float2 cm = tw[((u >> 6) * (kBorder + q)) & (kDft - 1)];
+            const float2 cn = tw[((u & 63) * (kBorder + q)) & (kDft - 1)];
+            const float pr = fmaf(d.x, cm.x, -d.y * cm.y), pim = fmaf(d.x, cm.y, d.y * cm.x);
+            st_shared_pair(smem_addr(ptab + (it * 16 + q) * 2), pack2(pr, pr), pack2(-pim, -pim));
+            etab[it * 32 + q] = cn.x;
+            etab[it * 32 + 16 + q] = cn.y;
         }
         __syncthreads();
         const uint32_t pbase = smem_addr(ptab) + (uint32_t)pi * 16u;
