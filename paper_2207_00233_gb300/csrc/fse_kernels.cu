@@ -144,23 +144,34 @@ struct FrameSrc {
         : fd(f), by(block / f.bw), bx(block % f.bw), self(block), gself(f.gob[block]),
           stage(st) {}
 
+    // The frame's fields, read once (the descriptor lives in global memory).
+    struct Frame {
+        int H, W, lb, bw, wstride;
+        const int32_t *gob;
+        const float *work;
+    };
+    __device__ __forceinline__ Frame frame() const {
+        return Frame{fd.H, fd.W, fd.lb, fd.bw, fd.wstride, fd.gob, fd.work};
+    }
+
     // Class and weight of the lost area sample at frame position (y, x):
     // R (an earlier-group block's concealed sample, read from the working
     // frame) or weight 0.
-    __device__ __forceinline__ void classify_lost(int y, int x, float rho, float delta, float &w,
-                                                  float &v) const {
-        const int cb = (y >> fd.lb) * fd.bw + (x >> fd.lb);
+    __device__ __forceinline__ void classify_lost(const Frame &f, int y, int x, float rho,
+                                                  float delta, float &w, float &v) const {
+        const int cb = (y >> f.lb) * f.bw + (x >> f.lb);
         if (cb != self) {
-            const int gc = fd.gob[cb];
+            const int gc = f.gob[cb];
             if (gc >= 0 && gc < gself) {
                 w = delta * rho;
-                v = __ldcg(fd.work + (size_t)y * fd.wstride + x);
+                v = __ldcg(f.work + (size_t)y * f.wstride + x);
             }
         }
     }
 
     __device__ void gather(float *xt, float *wt, const float *rho_tab, float delta) const {
-        const int B = 1 << fd.lb, M = B + 2 * kBorder;
+        const Frame f = frame();
+        const int B = 1 << f.lb, M = B + 2 * kBorder;
         const int y0 = by * B - kBorder, x0 = bx * B - kBorder;
         if (stage) {
             // tiles start at column x0 rounded down to a multiple of 16
@@ -171,13 +182,13 @@ struct FrameSrc {
                 const int m = p / kArea, n = p - m * kArea;
                 const int y = y0 + m, x = x0 + n;
                 float w = 0.f, v = 0.f;
-                if (m < M && n < M && y >= 0 && y < fd.H && x >= 0 && x < fd.W) {
+                if (m < M && n < M && y >= 0 && y < f.H && x >= 0 && x < f.W) {
                     const int q = m * kStageCols + n + dx;
                     if (!sm[q]) {
                         w = rho_tab[p];
                         v = (float)sl[q];
                     } else {
-                        classify_lost(y, x, rho_tab[p], delta, w, v);
+                        classify_lost(f, y, x, rho_tab[p], delta, w, v);
                     }
                 }
                 xt[m * kTileStride + n] = w * v;
@@ -185,17 +196,19 @@ struct FrameSrc {
             }
             return;
         }
+        const int stride = fd.stride;
+        const uint8_t *mask = fd.mask, *luma = fd.luma;
         for (int p = threadIdx.x; p < kArea * kArea; p += kThreads) {
             const int m = p / kArea, n = p - m * kArea;
             const int y = y0 + m, x = x0 + n;
             float w = 0.f, v = 0.f;
-            if (m < M && n < M && y >= 0 && y < fd.H && x >= 0 && x < fd.W) {
-                const size_t q = (size_t)y * fd.stride + x;
-                if (!fd.mask[q]) {
+            if (m < M && n < M && y >= 0 && y < f.H && x >= 0 && x < f.W) {
+                const size_t q = (size_t)y * stride + x;
+                if (!mask[q]) {
                     w = rho_tab[p];
-                    v = (float)fd.luma[q];
+                    v = (float)luma[q];
                 } else {
-                    classify_lost(y, x, rho_tab[p], delta, w, v);
+                    classify_lost(f, y, x, rho_tab[p], delta, w, v);
                 }
             }
             xt[m * kTileStride + n] = w * v;
@@ -206,8 +219,9 @@ struct FrameSrc {
     // Thread t holds the model value of sample (t / 16, t % 16) of the block.
     __device__ void store(float g) const {
         const int i = threadIdx.x >> 4, j = threadIdx.x & 15;
-        if (i >= (1 << fd.lb) || j >= (1 << fd.lb)) return;
-        const int y = (by << fd.lb) + i, x = (bx << fd.lb) + j;
+        const int lb = fd.lb;
+        if (i >= (1 << lb) || j >= (1 << lb)) return;
+        const int y = (by << lb) + i, x = (bx << lb) + j;
         if (y >= fd.H || x >= fd.W) return;
         const size_t q = (size_t)y * fd.stride + x;
         if (!fd.mask[q]) return;
