@@ -45,7 +45,7 @@ FP32_LANES = 128
 # DRAM bytes (read + write) of one k_persistent<FP32> launch on this workload,
 # from the ncu capture summarised in profiles/k_persistent_batch16_1080p_K200.md;
 # None while the kernel differs from the captured one
-TRAFFIC_BYTES_PER_LAUNCH = None
+TRAFFIC_BYTES_PER_LAUNCH = 190.454528e6 + 53.233664e6
 
 
 def parse():
@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="persistent launch with the occupancy limit of CTAs per SM, untuned "
+                         "(profiling: no candidate launches in the warm-up)")
     ap.add_argument("--precision", default="fp32",
                     choices=["fp32", "tf32", "bf16", "fp16", "bf16x3", "tf32x3"],
                     help="projection arithmetic of the main workload (profiling the "
@@ -403,7 +406,7 @@ def main():
     # the launch configuration is autotuned among bit-identical ones on the
     # first (warm-up) call, then reused; the inputs are resident before the
     # timed region, so a step may plan while the previous one still runs
-    ctx.fse_ctx_set_option(fse.FSE_OPT_AUTOTUNE, 1)
+    ctx.fse_ctx_set_option(fse.FSE_OPT_AUTOTUNE, 0 if args.no_autotune else 1)
     ctx.fse_ctx_set_option(fse.FSE_OPT_INPUTS_READY, 1)
     for _ in range(args.warmup):
         step()
@@ -533,7 +536,7 @@ def main():
                        "height": 1080, "width": 1920, "iters": K_ITERS, "order": "optimized",
                        "executor": ("persistent" if launch_cfg["executor"] == fse.FSE_EXEC_PERSISTENT
                                     else "levels"),
-                       "ctas_per_sm": launch_cfg["ctas_per_sm"], "autotuned": True,
+                       "ctas_per_sm": launch_cfg["ctas_per_sm"], "autotuned": not args.no_autotune,
                        "planning": "overlapped with the previous step (inputs ready)",
                        "precision": args.precision,
                        "lost_blocks_per_step": lost_blocks, "lost_pixels_per_step": lost_pixels,

@@ -325,8 +325,9 @@ int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_params *params,
  *                            results are identical: the persistent launch
  *                            with 1 .. (occupancy limit) CTAs per SM, or one
  *                            launch per dependency level.  The first call of
- *                            a shape runs and times every candidate (same
- *                            output bytes); later calls reuse the choice.
+ *                            a shape runs one untimed pass, then times every
+ *                            candidate twice (same output bytes); later
+ *                            calls reuse the choice.
  *                            0 (default): as requested.
  *   FSE_OPT_INPUTS_READY     1: the loss masks of each fse_conceal_batch call
  *                            are complete when the call is made (no work

@@ -834,7 +834,9 @@ extern "C" void fse_ctx_destroy(fse_ctx *ctx) {
 
 // FSE_OPT_AUTOTUNE: the first batch of a shape runs every launch
 // configuration with identical results and keeps the fastest (device time
-// from the call's start to its last launch, planning included).
+// from the call's start to its last launch, planning included): one
+// untimed pass first (first-use costs), then each candidate twice, the
+// faster run counting.
 static int autotuned_batch(fse_ctx *ctx, const fse_frame *frames, int n,
                            const fse_params *params, cudaStream_t stream) {
     long long samples = 0;
@@ -860,7 +862,11 @@ static int autotuned_batch(fse_ctx *ctx, const fse_frame *frames, int n,
     float best = -1.f;
     std::pair<int, int> choice = cand.front();
     int rc = FSE_OK;
-    for (const auto &c : cand) {
+    p.executor = cand.front().first;  // untimed pass
+    rc = run_batch(ctx, ctx->ws, frames, n, &p, stream, nullptr, cand.front().second);
+    if (!rc) rc = read_status(ctx, ctx->ws, stream);
+    for (size_t k = 0; k < 2 * cand.size() && !rc; ++k) {
+        const auto &c = cand[k % cand.size()];
         p.executor = c.first;
         if (cudaEventRecord(e0, stream) != cudaSuccess) {
             rc = FSE_ECUDA;
