@@ -235,7 +235,9 @@ int fse_poll(fse_ctx *ctx, uint64_t ticket, int *done, fse_stats *out);
 int fse_drain(fse_ctx *ctx, int timeout_ms);
 
 /* Device-side statistics of the last fse_conceal_batch / _host call:
- * lost blocks, groups (max over frames) and kernel launches enqueued. */
+ * lost blocks, groups (max over frames) and kernel launches enqueued (the
+ * extrapolation launches, plus one for the block-loss map kernel when the
+ * maps were built on the device). */
 int fse_last_batch_info(fse_ctx *ctx, int *lost_blocks, int *groups,
                         int *launches);
 

@@ -403,27 +403,31 @@ static int poll_status_ring(Workspace &ws, int wait_slot) {
     return rc;
 }
 
-int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
-                   const fse_params *p, cudaStream_t stream,
-                   const std::vector<std::vector<uint8_t>> *host_lost, int ctas_per_sm) {
-    int rc = FSE_OK;
-    const float *rho_tab = ctx->rho_table(p->rho, p->block, &rc);
-    if (!rho_tab) return rc;
-    const uint4 *frags = ctx->frag_table(p->precision, &rc);
-    if (rc) return rc;
-    // The staging buffers of the previous batch on this workspace must have
-    // been consumed before they are overwritten.
-    if (ws.staged) {
-        CK(cudaEventSynchronize(ws.staged));
-    }
+namespace {
 
-    // ---- geometry ----
-    std::vector<FrameDesc> fd(n);
-    std::vector<int> lost_off(n + 1, 0);
+// Host-side state of one batch, from the frames to the work items.
+struct Batch {
+    std::vector<FrameDesc> fd;
+    std::vector<int> lost_off;  // first block of each frame in the flat maps
+    int nblocks = 0;
+    std::vector<uint8_t> lost;  // block-loss maps
+    std::vector<int32_t> gob;   // group of each block (-1: nothing to do)
+    std::vector<std::vector<int32_t>> gptr, ids;  // groups of each frame
+    std::vector<FrameDepths> depths;
+    int max_groups = 0, lost_blocks = 0;
+    std::vector<int2> items;       // claim or launch order
+    std::vector<int> level_start;  // launch boundaries (groups executor)
+    bool map_kernel = false;       // the loss maps were built on the device
+};
+
+// Frame descriptors and the workspace buffers they point into.
+int setup_frames(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
+                 const fse_params *p, Batch &b) {
+    b.fd.assign(n, FrameDesc{});
+    b.lost_off.assign(n + 1, 0);
     size_t work_floats = 0;
-    int max_rows_x_bw = 0;
     for (int i = 0; i < n; ++i) {
-        FrameDesc &d = fd[i];
+        FrameDesc &d = b.fd[i];
         d.luma = frames[i].luma;
         d.mask = frames[i].loss_mask;
         d.out = frames[i].out;
@@ -436,53 +440,57 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
         d.tmaps = nullptr;
         d.bh = (d.H + p->block - 1) / p->block;
         d.bw = (d.W + p->block - 1) / p->block;
-        lost_off[i + 1] = lost_off[i] + d.bh * d.bw;
+        b.lost_off[i + 1] = b.lost_off[i] + d.bh * d.bw;
         work_floats += (size_t)d.H * d.wstride;
-        max_rows_x_bw = std::max(max_rows_x_bw, d.H * d.bw);
     }
-    const int nblocks = lost_off[n];
-
-    rc = ctx->dev_reserve(ws.frames, sizeof(FrameDesc) * n);
+    b.nblocks = b.lost_off[n];
+    int rc = ctx->dev_reserve(ws.frames, sizeof(FrameDesc) * n);
     if (!rc && ctx->keep_trace)
         rc = ctx->dev_reserve(ws.trace, sizeof(int16_t) * std::max<size_t>(
-                                            (size_t)nblocks * std::max(p->iters, 1), 1));
+                                            (size_t)b.nblocks * std::max(p->iters, 1), 1));
     if (!rc) rc = ctx->dev_reserve(ws.work, sizeof(float) * work_floats);
-    if (!rc) rc = ctx->dev_reserve(ws.lost, nblocks);
+    if (!rc) rc = ctx->dev_reserve(ws.lost, b.nblocks);
     if (!rc) rc = ctx->dev_reserve(ws.lost_off, sizeof(int) * (n + 1));
-    if (!rc) rc = ctx->dev_reserve(ws.gob, sizeof(int32_t) * nblocks);
+    if (!rc) rc = ctx->dev_reserve(ws.gob, sizeof(int32_t) * b.nblocks);
     if (!rc) rc = ctx->dev_reserve(ws.status, sizeof(int) * 4);
     if (rc) return rc;
-    {
-        float *wp = static_cast<float *>(ws.work.ptr);
-        for (int i = 0; i < n; ++i) {
-            fd[i].work = wp;
-            fd[i].gob = static_cast<int32_t *>(ws.gob.ptr) + lost_off[i];
-            fd[i].trace = ctx->keep_trace ? static_cast<int16_t *>(ws.trace.ptr) +
-                                                (size_t)lost_off[i] * p->iters
-                                          : nullptr;
-            wp += (size_t)fd[i].H * fd[i].wstride;
-        }
+    float *wp = static_cast<float *>(ws.work.ptr);
+    for (int i = 0; i < n; ++i) {
+        b.fd[i].work = wp;
+        b.fd[i].gob = static_cast<int32_t *>(ws.gob.ptr) + b.lost_off[i];
+        b.fd[i].trace = ctx->keep_trace ? static_cast<int16_t *>(ws.trace.ptr) +
+                                              (size_t)b.lost_off[i] * p->iters
+                                        : nullptr;
+        wp += (size_t)b.fd[i].H * b.fd[i].wstride;
     }
+    return FSE_OK;
+}
 
-    // ---- block-loss maps ----
-    std::vector<uint8_t> lost_h(nblocks);
-    int prev_error = 0;
+// Block-loss maps: given by the caller (host frames), built on the host from
+// a side-stream copy of the masks (FSE_OPT_INPUTS_READY), or built on the
+// device in stream order and read back (which also reports a failed wait of
+// the previous batch).
+int block_loss_maps(fse_ctx *ctx, Workspace &ws, int n, const fse_params *p, cudaStream_t stream,
+                    const std::vector<std::vector<uint8_t>> *host_lost, Batch &b) {
+    const std::vector<FrameDesc> &fd = b.fd;
+    b.lost.assign(b.nblocks, 0);
+    int rc = FSE_OK;
     if (host_lost) {
         for (int i = 0; i < n; ++i)
-            std::memcpy(lost_h.data() + lost_off[i], (*host_lost)[i].data(),
+            std::memcpy(b.lost.data() + b.lost_off[i], (*host_lost)[i].data(),
                         (size_t)fd[i].bh * fd[i].bw);
-    } else if (ctx->inputs_ready) {
+        return FSE_OK;
+    }
+    if (ctx->inputs_ready) {
         // The masks are complete now: copy them to the host on a side stream,
         // not behind the work queued on `stream` (typically the previous
         // batch, still running), and build the maps there, so that planning
         // overlaps that work.
         if ((rc = poll_status_ring(ws, -1))) return rc;
         if (!ws.side) CK(cudaStreamCreateWithFlags(&ws.side, cudaStreamNonBlocking));
-        size_t total = 0;
         std::vector<size_t> moff(n + 1, 0);
         for (int i = 0; i < n; ++i) moff[i + 1] = moff[i] + (size_t)fd[i].W * fd[i].H;
-        total = moff[n];
-        if ((rc = ctx->host_reserve(ws.mstage, std::max<size_t>(total, 1)))) return rc;
+        if ((rc = ctx->host_reserve(ws.mstage, std::max<size_t>(moff[n], 1)))) return rc;
         uint8_t *ms = static_cast<uint8_t *>(ws.mstage.ptr);
         for (int i = 0; i < n; ++i)
             CK(cudaMemcpy2DAsync(ms + moff[i], fd[i].W, fd[i].mask, fd[i].stride, fd[i].W,
@@ -491,137 +499,128 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
         ctx->pool.run(n, [&](int i) {
             const fse_frame h{nullptr, nullptr, ms + moff[i], fd[i].W, fd[i].H, fd[i].W};
             const std::vector<uint8_t> m = host_block_loss(h, p->block);
-            std::memcpy(lost_h.data() + lost_off[i], m.data(), m.size());
+            std::memcpy(b.lost.data() + b.lost_off[i], m.data(), m.size());
         });
-    } else {
-        rc = ctx->host_reserve(ws.stage, sizeof(FrameDesc) * n + sizeof(int) * (n + 1) +
-                                             nblocks + 64);
-        if (rc) return rc;
-        char *st = static_cast<char *>(ws.stage.ptr);
-        std::memcpy(st, fd.data(), sizeof(FrameDesc) * n);
-        std::memcpy(st + sizeof(FrameDesc) * n, lost_off.data(), sizeof(int) * (n + 1));
-        CK(cudaMemcpyAsync(ws.frames.ptr, st, sizeof(FrameDesc) * n, cudaMemcpyHostToDevice,
-                           stream));
-        CK(cudaMemcpyAsync(ws.lost_off.ptr, st + sizeof(FrameDesc) * n, sizeof(int) * (n + 1),
-                           cudaMemcpyHostToDevice, stream));
-        CK(cudaMemsetAsync(ws.lost.ptr, 0, nblocks, stream));
-        CK(launch_block_loss(static_cast<FrameDesc *>(ws.frames.ptr), n, max_rows_x_bw,
-                             static_cast<uint8_t *>(ws.lost.ptr),
-                             static_cast<int *>(ws.lost_off.ptr), stream));
-        uint8_t *lost_stage = reinterpret_cast<uint8_t *>(st + sizeof(FrameDesc) * n +
-                                                          sizeof(int) * (n + 1));
-        int *err_stage = reinterpret_cast<int *>(
-            (reinterpret_cast<uintptr_t>(lost_stage + nblocks) + 15) & ~(uintptr_t)15);
-        CK(cudaMemcpyAsync(lost_stage, ws.lost.ptr, nblocks, cudaMemcpyDeviceToHost, stream));
-        if (ws.status_live) {
-            CK(cudaMemcpyAsync(err_stage, static_cast<int *>(ws.status.ptr) + 1, sizeof(int),
-                               cudaMemcpyDeviceToHost, stream));
-        }
-        CK(cudaStreamSynchronize(stream));
-        std::memcpy(lost_h.data(), lost_stage, nblocks);
-        if (ws.status_live) prev_error = *err_stage;
+        return FSE_OK;
     }
-    if (prev_error) {
+    int max_rows_x_bw = 0;
+    for (int i = 0; i < n; ++i) max_rows_x_bw = std::max(max_rows_x_bw, fd[i].H * fd[i].bw);
+    rc = ctx->host_reserve(ws.stage, sizeof(FrameDesc) * n + sizeof(int) * (n + 1) +
+                                         b.nblocks + 64);
+    if (rc) return rc;
+    char *st = static_cast<char *>(ws.stage.ptr);
+    std::memcpy(st, fd.data(), sizeof(FrameDesc) * n);
+    std::memcpy(st + sizeof(FrameDesc) * n, b.lost_off.data(), sizeof(int) * (n + 1));
+    CK(cudaMemcpyAsync(ws.frames.ptr, st, sizeof(FrameDesc) * n, cudaMemcpyHostToDevice,
+                       stream));
+    CK(cudaMemcpyAsync(ws.lost_off.ptr, st + sizeof(FrameDesc) * n, sizeof(int) * (n + 1),
+                       cudaMemcpyHostToDevice, stream));
+    CK(cudaMemsetAsync(ws.lost.ptr, 0, b.nblocks, stream));
+    CK(launch_block_loss(static_cast<FrameDesc *>(ws.frames.ptr), n, max_rows_x_bw,
+                         static_cast<uint8_t *>(ws.lost.ptr),
+                         static_cast<int *>(ws.lost_off.ptr), stream));
+    b.map_kernel = true;
+    uint8_t *lost_stage =
+        reinterpret_cast<uint8_t *>(st + sizeof(FrameDesc) * n + sizeof(int) * (n + 1));
+    int *err_stage = reinterpret_cast<int *>(
+        (reinterpret_cast<uintptr_t>(lost_stage + b.nblocks) + 15) & ~(uintptr_t)15);
+    CK(cudaMemcpyAsync(lost_stage, ws.lost.ptr, b.nblocks, cudaMemcpyDeviceToHost, stream));
+    if (ws.status_live)
+        CK(cudaMemcpyAsync(err_stage, static_cast<int *>(ws.status.ptr) + 1, sizeof(int),
+                           cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    std::memcpy(b.lost.data(), lost_stage, b.nblocks);
+    if (ws.status_live && *err_stage) {
         ws.status_live = false;
         return FSE_ETIMEDOUT;
     }
+    return FSE_OK;
+}
 
-    // ---- processing order per frame (host, integer; frames in parallel) ----
-    // and the dependency depths of each frame's lost blocks
-    std::vector<int32_t> gob_h(nblocks);
-    std::vector<std::vector<int32_t>> frame_gptr(n), frame_ids(n);
-    std::vector<FrameDepths> depths(n);
+// Processing order of every frame (Algorithm 1 or line scan) and the
+// dependency depths of its lost blocks, frames on the worker pool.
+int plan_frames(fse_ctx *ctx, int n, const fse_params *p, Batch &b) {
+    b.gob.assign(b.nblocks, -1);
+    b.gptr.assign(n, {});
+    b.ids.assign(n, {});
+    b.depths.assign(n, FrameDepths{});
     std::vector<int> plan_rc(n, FSE_OK);
     const int rad = kBorder >> block_log2(p->block);
-    auto plan_one = [&](int i) {
-        const int nb = fd[i].bh * fd[i].bw;
+    ctx->pool.run(n, [&](int i) {
+        const FrameDesc &d = b.fd[i];
+        const int nb = d.bh * d.bw;
         std::vector<int32_t> gptr(nb + 1, 0), ids(nb, 0);
         int32_t ng = 0;
-        plan_rc[i] = fse_plan_order(fd[i].bw, fd[i].bh, lost_h.data() + lost_off[i], p->order,
-                                    gob_h.data() + lost_off[i], gptr.data(), ids.data(), &ng);
+        plan_rc[i] = fse_plan_order(d.bw, d.bh, b.lost.data() + b.lost_off[i], p->order,
+                                    b.gob.data() + b.lost_off[i], gptr.data(), ids.data(), &ng);
         if (plan_rc[i]) return;
-        frame_gptr[i].assign(gptr.begin(), gptr.begin() + ng + 1);
-        frame_ids[i].assign(ids.begin(), ids.begin() + gptr[ng]);
-        FrameDepths &f = depths[i];
-        f.bw = fd[i].bw;
-        f.bh = fd[i].bh;
-        f.gob = gob_h.data() + lost_off[i];
-        f.ids = frame_ids[i].data();
-        f.n = (int)frame_ids[i].size();
+        b.gptr[i].assign(gptr.begin(), gptr.begin() + ng + 1);
+        b.ids[i].assign(ids.begin(), ids.begin() + gptr[ng]);
+        FrameDepths &f = b.depths[i];
+        f.bw = d.bw;
+        f.bh = d.bh;
+        f.gob = b.gob.data() + b.lost_off[i];
+        f.ids = b.ids[i].data();
+        f.n = (int)b.ids[i].size();
         frame_depths(f, rad);
-    };
-    ctx->pool.run(n, plan_one);
-    int max_groups = 0, lost_blocks = 0;
+    });
+    b.max_groups = b.lost_blocks = 0;
     for (int i = 0; i < n; ++i) {
         if (plan_rc[i]) return plan_rc[i];
-        const int ng = (int)frame_gptr[i].size() - 1;
-        max_groups = std::max(max_groups, ng);
-        lost_blocks += frame_gptr[i][ng];
+        const int ng = (int)b.gptr[i].size() - 1;
+        b.max_groups = std::max(b.max_groups, ng);
+        b.lost_blocks += b.gptr[i][ng];
     }
+    return FSE_OK;
+}
 
-    // ---- work items: one launch per dependency level, or the claim order
-    // of the persistent CTAs ----
-    const bool persistent = p->executor == FSE_EXEC_PERSISTENT;
-    int grid = 0;
-    int per_sm = 0;
+// Work items: the persistent CTAs' claim order (delayed height order), one
+// launch per dependency level, or one launch per plan group.
+void claim_order(fse_ctx *ctx, int n, bool persistent, int grid, Batch &b) {
+    b.items.clear();
+    b.level_start.clear();
     if (persistent) {
-        per_sm = max_resident_ctas(p->iters);
-        const int cap = ctas_per_sm >= 0 ? ctas_per_sm : ctx->persistent_ctas;
-        if (cap > 0) per_sm = std::min(per_sm, cap);
-        grid = std::min<int>(lost_blocks, ctx->num_sms * per_sm);
-    }
-    ws.executor = p->executor;
-    ws.ctas_per_sm = per_sm;
-    std::vector<int2> items;
-    std::vector<int> level_start;
-    if (persistent) {
-        delay_claims(depths, std::max(grid, 1), items,
-                     [&](int n, const std::function<void(int)> &fn) { ctx->pool.run(n, fn); });
+        delay_claims(b.depths, std::max(grid, 1), b.items,
+                     [&](int m, const std::function<void(int)> &fn) { ctx->pool.run(m, fn); });
     } else if (ctx->group_launches) {
-        // one launch per plan group: group g of every frame, frame by frame
-        items.reserve(lost_blocks);
-        level_start.assign(1, 0);
-        for (int g = 0; g < max_groups; ++g) {
+        // group g of every frame, frame by frame
+        b.items.reserve(b.lost_blocks);
+        b.level_start.assign(1, 0);
+        for (int g = 0; g < b.max_groups; ++g) {
             for (int i = 0; i < n; ++i) {
-                const auto &gp = frame_gptr[i];
+                const auto &gp = b.gptr[i];
                 if (g + 1 >= (int)gp.size()) continue;
-                for (int j = gp[g]; j < gp[g + 1]; ++j) items.push_back(make_int2(i, frame_ids[i][j]));
+                for (int j = gp[g]; j < gp[g + 1]; ++j) b.items.push_back(make_int2(i, b.ids[i][j]));
             }
-            level_start.push_back((int)items.size());
+            b.level_start.push_back((int)b.items.size());
         }
     } else {
-        level_claims(depths, items, level_start);
+        level_claims(b.depths, b.items, b.level_start);
     }
-    const int n_launch_levels = persistent ? 0 : (int)level_start.size() - 1;
+}
 
-    // ---- uploads ----
-    const size_t n_items = items.size();
-    rc = ctx->dev_reserve(ws.items, sizeof(int2) * std::max<size_t>(n_items, 1));
-    if (!rc && persistent) rc = ctx->dev_reserve(ws.done, sizeof(uint32_t) * nblocks);
+// Descriptors, group maps, items and TMA descriptors to the device through
+// the pinned staging buffer; completion flags cleared.
+int upload_batch(fse_ctx *ctx, Workspace &ws, int n, bool persistent, cudaStream_t stream,
+                 Batch &b) {
+    const size_t n_items = b.items.size();
+    int rc = ctx->dev_reserve(ws.items, sizeof(int2) * std::max<size_t>(n_items, 1));
+    if (!rc && persistent) rc = ctx->dev_reserve(ws.done, sizeof(uint32_t) * b.nblocks);
     if (rc) return rc;
-    int stuck_item = -1;
-    if (persistent && ctx->test_stuck_dep && n_items > 0) {
-        stuck_item = (int)n_items - 1;  // waits on a flag nothing sets
-        ctx->test_stuck_dep = false;
-    }
-    {
-        uint32_t *dp = static_cast<uint32_t *>(ws.done.ptr);
-        for (int i = 0; i < n; ++i) fd[i].done = persistent ? dp + lost_off[i] : nullptr;
-    }
+    uint32_t *dp = static_cast<uint32_t *>(ws.done.ptr);
+    for (int i = 0; i < n; ++i) b.fd[i].done = persistent ? dp + b.lost_off[i] : nullptr;
     // TMA descriptors (frames whose buffers allow it)
     std::vector<CUtensorMap> maps((size_t)kMapsPerFrame * n);
     if (n_items > 0) {
-        rc = ctx->dev_reserve(ws.tmaps, sizeof(CUtensorMap) * kMapsPerFrame * n);
-        if (rc) return rc;
+        if ((rc = ctx->dev_reserve(ws.tmaps, sizeof(CUtensorMap) * kMapsPerFrame * n))) return rc;
         const char *mp = static_cast<const char *>(ws.tmaps.ptr);
         for (int i = 0; i < n; ++i)
-            if (encode_frame_maps(fd[i], &maps[(size_t)kMapsPerFrame * i]))
-                fd[i].tmaps = mp + sizeof(CUtensorMap) * kMapsPerFrame * i;
+            if (encode_frame_maps(b.fd[i], &maps[(size_t)kMapsPerFrame * i]))
+                b.fd[i].tmaps = mp + sizeof(CUtensorMap) * kMapsPerFrame * i;
     }
-    const size_t stage_bytes = sizeof(FrameDesc) * n + sizeof(int32_t) * nblocks +
+    const size_t stage_bytes = sizeof(FrameDesc) * n + sizeof(int32_t) * b.nblocks +
                                sizeof(int2) * n_items + sizeof(CUtensorMap) * maps.size() + 256;
-    rc = ctx->host_reserve(ws.stage, stage_bytes);
-    if (rc) return rc;
+    if ((rc = ctx->host_reserve(ws.stage, stage_bytes))) return rc;
     char *st = static_cast<char *>(ws.stage.ptr);
     size_t off = 0;
     auto put = [&](void *dev, const void *src, size_t bytes) -> int {
@@ -634,15 +633,55 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
         off = (off + bytes + 15) & ~(size_t)15;
         return FSE_OK;
     };
-    rc = put(ws.frames.ptr, fd.data(), sizeof(FrameDesc) * n);
-    if (!rc) rc = put(ws.gob.ptr, gob_h.data(), sizeof(int32_t) * nblocks);
-    if (!rc) rc = put(ws.items.ptr, items.data(), sizeof(int2) * n_items);
+    rc = put(ws.frames.ptr, b.fd.data(), sizeof(FrameDesc) * n);
+    if (!rc) rc = put(ws.gob.ptr, b.gob.data(), sizeof(int32_t) * b.nblocks);
+    if (!rc) rc = put(ws.items.ptr, b.items.data(), sizeof(int2) * n_items);
     if (!rc && n_items > 0) rc = put(ws.tmaps.ptr, maps.data(), sizeof(CUtensorMap) * maps.size());
     if (rc) return rc;
-    if (persistent && nblocks > 0)
-        CK(cudaMemsetAsync(ws.done.ptr, 0, sizeof(uint32_t) * nblocks, stream));
+    if (persistent && b.nblocks > 0)
+        CK(cudaMemsetAsync(ws.done.ptr, 0, sizeof(uint32_t) * b.nblocks, stream));
     if (!ws.staged) CK(cudaEventCreateWithFlags(&ws.staged, cudaEventDisableTiming));
     CK(cudaEventRecord(ws.staged, stream));
+    return FSE_OK;
+}
+
+}  // namespace
+
+int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
+                   const fse_params *p, cudaStream_t stream,
+                   const std::vector<std::vector<uint8_t>> *host_lost, int ctas_per_sm) {
+    int rc = FSE_OK;
+    const float *rho_tab = ctx->rho_table(p->rho, p->block, &rc);
+    if (!rho_tab) return rc;
+    const uint4 *frags = ctx->frag_table(p->precision, &rc);
+    if (rc) return rc;
+    // The staging buffers of the previous batch on this workspace must have
+    // been consumed before they are overwritten.
+    if (ws.staged) CK(cudaEventSynchronize(ws.staged));
+
+    Batch b;
+    if ((rc = setup_frames(ctx, ws, frames, n, p, b))) return rc;
+    if ((rc = block_loss_maps(ctx, ws, n, p, stream, host_lost, b))) return rc;
+    if ((rc = plan_frames(ctx, n, p, b))) return rc;
+
+    const bool persistent = p->executor == FSE_EXEC_PERSISTENT;
+    int grid = 0, per_sm = 0;
+    if (persistent) {
+        per_sm = max_resident_ctas(p->iters);
+        const int cap = ctas_per_sm >= 0 ? ctas_per_sm : ctx->persistent_ctas;
+        if (cap > 0) per_sm = std::min(per_sm, cap);
+        grid = std::min<int>(b.lost_blocks, ctx->num_sms * per_sm);
+    }
+    ws.executor = p->executor;
+    ws.ctas_per_sm = per_sm;
+    claim_order(ctx, n, persistent, grid, b);
+    const size_t n_items = b.items.size();
+    int stuck_item = -1;
+    if (persistent && ctx->test_stuck_dep && n_items > 0) {
+        stuck_item = (int)n_items - 1;  // waits on a flag nothing sets
+        ctx->test_stuck_dep = false;
+    }
+    if ((rc = upload_batch(ctx, ws, n, persistent, stream, b))) return rc;
 
     // ---- outputs start as copies of the inputs ----
     for (int i = 0; i < n; ++i) {
@@ -658,7 +697,7 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
                      status + 1};
     const FrameDesc *fdev = static_cast<const FrameDesc *>(ws.frames.ptr);
     const float2 *tw_tab = static_cast<const float2 *>(ctx->tw_dev.ptr);
-    int launches = 1;  // block-loss map
+    int launches = b.map_kernel ? 1 : 0;
     ws.k_timed = false;
     if (n_items > 0) {
         const int kslot = ws.k_pos;
@@ -680,9 +719,9 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
             launches += 1;
         } else {
             const int2 *idev = static_cast<const int2 *>(ws.items.ptr);
-            for (int l = 0; l < n_launch_levels; ++l) {
-                const int cnt = level_start[l + 1] - level_start[l];
-                CK(launch_group(fdev, idev + level_start[l], cnt, kp, rho_tab, tw_tab,
+            for (size_t l = 0; l + 1 < b.level_start.size(); ++l) {
+                const int cnt = b.level_start[l + 1] - b.level_start[l];
+                CK(launch_group(fdev, idev + b.level_start[l], cnt, kp, rho_tab, tw_tab,
                                 p->precision, stream));
                 launches += 1;
             }
@@ -708,24 +747,25 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
             ws.status_live = false;
         }
     }
-    ws.lost_blocks = lost_blocks;
-    ws.groups = max_groups;
+
+    // ---- what the inspection entry points read back ----
+    ws.lost_blocks = b.lost_blocks;
+    ws.groups = b.max_groups;
     ws.launches = launches;
     ws.trace_ptr.assign(n, nullptr);
     ws.trace_len.assign(n, 0);
-    for (int i = 0; i < n; ++i) {
-        ws.trace_ptr[i] = fd[i].trace;
-        ws.trace_len[i] = fd[i].trace ? (size_t)fd[i].bh * fd[i].bw * p->iters : 0;
-    }
     ws.work_ptr.resize(n);
     ws.work_w.resize(n);
     ws.work_h.resize(n);
     ws.work_stride.resize(n);
     for (int i = 0; i < n; ++i) {
-        ws.work_ptr[i] = fd[i].work;
-        ws.work_w[i] = fd[i].W;
-        ws.work_h[i] = fd[i].H;
-        ws.work_stride[i] = fd[i].wstride;
+        const FrameDesc &d = b.fd[i];
+        ws.trace_ptr[i] = d.trace;
+        ws.trace_len[i] = d.trace ? (size_t)d.bh * d.bw * p->iters : 0;
+        ws.work_ptr[i] = d.work;
+        ws.work_w[i] = d.W;
+        ws.work_h[i] = d.H;
+        ws.work_stride[i] = d.wstride;
     }
     return FSE_OK;
 }
