@@ -191,10 +191,35 @@ int fse_conceal_batch(fse_ctx *ctx, const fse_frame *frames, int n,
                       const fse_params *params, void *cuda_stream);
 
 /* Same as fse_conceal_batch for frames in HOST memory: copies the inputs to
- * the device, conceals, copies `out` back and synchronises `cuda_stream`
- * before returning (so it reports FSE_ETIMEDOUT directly). */
+ * the device, conceals, copies `out` back and returns when `out` holds the
+ * result (so it reports FSE_ETIMEDOUT directly).  The block-loss maps come
+ * from the host masks.  The inputs are copied in on a stream of the
+ * context, the extrapolation runs on `cuda_stream`, the outputs are copied
+ * back on another stream of the context.  Host buffers should be
+ * page-locked for the copies to run asynchronously. */
 int fse_conceal_batch_host(fse_ctx *ctx, const fse_frame *frames, int n,
                            const fse_params *params, void *cuda_stream);
+
+/* Asynchronous form of fse_conceal_batch_host: enqueues the copies, plans
+ * the batch on the host and enqueues its launch, then returns; *ticket
+ * names the batch for fse_wait_batch.  Two batches can be in flight: the
+ * host planning and the copies of one overlap the extrapolation of the
+ * other.  A call made while two are in flight first waits for the older
+ * one (its status is kept for its fse_wait_batch; the statuses of the 64
+ * most recent unwaited batches are kept).  The frames' host buffers (luma,
+ * loss_mask, out) must stay valid and unmodified (out: unread) until
+ * fse_wait_batch(ticket) returns; they should be page-locked, since a copy
+ * to or from pageable memory makes the call wait for it.
+ * Errors: as fse_conceal_batch_host, FSE_EINVAL for a NULL ticket. */
+int fse_conceal_batch_host_async(fse_ctx *ctx, const fse_frame *frames, int n,
+                                 const fse_params *params, void *cuda_stream,
+                                 uint64_t *ticket);
+
+/* Wait until the batch `ticket` of fse_conceal_batch_host_async has written
+ * its outputs to host memory and return its status (FSE_ETIMEDOUT if a
+ * device wait of its launch failed, FSE_ECUDA).  A ticket can be waited for
+ * once.  Errors: FSE_ENOTFOUND for an unknown or already waited ticket. */
+int fse_wait_batch(fse_ctx *ctx, uint64_t ticket);
 
 /* FSE of n pre-gathered areas (DEVICE pointers), for inspection and parity
  * tests of the per-block computation alone.  The area is M x M with

@@ -23,7 +23,8 @@ FSE_MAX_ITERS = 1024
 
 EXPORTED = [
     "fse_plan_order", "fse_plan_claims", "fse_ctx_create", "fse_ctx_destroy", "fse_conceal_batch",
-    "fse_conceal_batch_host", "fse_extrapolate_areas", "fse_submit", "fse_poll",
+    "fse_conceal_batch_host", "fse_conceal_batch_host_async", "fse_wait_batch",
+    "fse_extrapolate_areas", "fse_submit", "fse_poll",
     "fse_drain", "fse_last_batch_info", "fse_last_batch_config", "fse_ctx_set_option", "fse_copy_work", "fse_copy_trace", "fse_last_kernel_ms", "fse_recent_kernel_ms", "fse_conceal_frame_noalloc", "fse_measure_peaks", "fse_strerror",
 ]
 FSE_OPT_SPIN_LIMIT, FSE_OPT_PERSISTENT_CTAS, FSE_OPT_SERVE_SLOTS = 1, 2, 3
@@ -80,6 +81,9 @@ def lib() -> ctypes.CDLL:
     L.fse_conceal_batch.argtypes = [vp, ctypes.POINTER(fse_frame), cint,
                                     ctypes.POINTER(fse_params), vp]
     L.fse_conceal_batch_host.argtypes = L.fse_conceal_batch.argtypes
+    L.fse_conceal_batch_host_async.argtypes = L.fse_conceal_batch.argtypes + [
+        ctypes.POINTER(ctypes.c_uint64)]
+    L.fse_wait_batch.argtypes = [vp, ctypes.c_uint64]
     L.fse_extrapolate_areas.argtypes = [vp, vp, vp, cint, ctypes.POINTER(fse_params), vp, vp,
                                         vp, vp, vp]
     L.fse_submit.argtypes = [vp, ctypes.POINTER(fse_frame), ctypes.POINTER(fse_params),
@@ -111,6 +115,25 @@ def strerror(code: int) -> str:
 def _check(rc: int, where: str) -> None:
     if rc != FSE_OK:
         raise FseError(rc, where)
+
+
+def _host_frames(frames):
+    """fse_frame array of host (luma, mask, out) uint8 arrays or CPU tensors."""
+    arr = (fse_frame * len(frames))()
+    for i, (luma, mask, out) in enumerate(frames):
+        ptrs = []
+        for a in (luma, mask, out):
+            if isinstance(a, np.ndarray):
+                if a.dtype != np.uint8 or not a.flags["C_CONTIGUOUS"] or a.ndim != 2:
+                    raise ValueError("host frames must be C-contiguous 2-D uint8 arrays")
+                ptrs.append(a.ctypes.data)
+            else:
+                if not a.is_contiguous() or a.dim() != 2:
+                    raise ValueError("host tensors must be contiguous 2-D")
+                ptrs.append(a.data_ptr())
+        h, w = luma.shape
+        arr[i] = fse_frame(ptrs[0], ptrs[2], ptrs[1], w, h, w)
+    return arr
 
 
 def make_params(iters: int = 200, rho: float = 0.7, delta: float = 0.2, gamma: float = 0.5,
@@ -228,22 +251,22 @@ class Context:
     def fse_conceal_batch_host(self, frames, params: fse_params, stream=None) -> None:
         """frames: list of (luma, mask, out) C-contiguous uint8 numpy arrays
         (or pinned CPU tensors); out is written before the call returns."""
-        arr = (fse_frame * len(frames))()
-        for i, (luma, mask, out) in enumerate(frames):
-            ptrs = []
-            for a in (luma, mask, out):
-                if isinstance(a, np.ndarray):
-                    if a.dtype != np.uint8 or not a.flags["C_CONTIGUOUS"] or a.ndim != 2:
-                        raise ValueError("host frames must be C-contiguous 2-D uint8 arrays")
-                    ptrs.append(a.ctypes.data)
-                else:
-                    if not a.is_contiguous() or a.dim() != 2:
-                        raise ValueError("host tensors must be contiguous 2-D")
-                    ptrs.append(a.data_ptr())
-            h, w = luma.shape
-            arr[i] = fse_frame(ptrs[0], ptrs[2], ptrs[1], w, h, w)
-        _check(lib().fse_conceal_batch_host(self.handle, arr, len(frames), ctypes.byref(params),
-                                            _stream_handle(stream)), "fse_conceal_batch_host")
+        _check(lib().fse_conceal_batch_host(self.handle, _host_frames(frames), len(frames),
+                                            ctypes.byref(params), _stream_handle(stream)),
+               "fse_conceal_batch_host")
+
+    def fse_conceal_batch_host_async(self, frames, params: fse_params, stream=None) -> int:
+        """As fse_conceal_batch_host, but returns a ticket once the batch is
+        enqueued; the buffers must stay alive until fse_wait_batch(ticket)."""
+        t = ctypes.c_uint64(0)
+        _check(lib().fse_conceal_batch_host_async(self.handle, _host_frames(frames), len(frames),
+                                                  ctypes.byref(params), _stream_handle(stream),
+                                                  ctypes.byref(t)),
+               "fse_conceal_batch_host_async")
+        return t.value
+
+    def fse_wait_batch(self, ticket: int) -> None:
+        _check(lib().fse_wait_batch(self.handle, ctypes.c_uint64(ticket)), "fse_wait_batch")
 
     def fse_extrapolate_areas(self, area_f, area_cls, params: fse_params, g_out, u_out=None,
                               dc_out=None, r_out=None, stream=None) -> None:

@@ -23,7 +23,7 @@ NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["fse_kernels.cu", "fse_noalloc.cu", "fse_peaks.cu"]
-CPP_SOURCES = ["fse_api.cpp", "fse_serve.cpp", "fse_plan.cpp", "fse_sched.cpp"]
+CPP_SOURCES = ["fse_api.cpp", "fse_hostbatch.cpp", "fse_serve.cpp", "fse_plan.cpp", "fse_sched.cpp"]
 HEADERS = ["fse_internal.h", "fse_ctx.h"]
 
 

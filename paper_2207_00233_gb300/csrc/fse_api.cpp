@@ -249,7 +249,7 @@ int fse::check_params(const fse_params *p) {
     return FSE_OK;
 }
 
-static int check_frame(const fse_frame &f) {
+int fse::check_frame(const fse_frame &f) {
     if (!f.luma || !f.out || !f.loss_mask) return FSE_EINVAL;
     if (f.width <= 0 || f.height <= 0 || f.stride < f.width) return FSE_EINVAL;
     if ((long long)f.width * f.height > (1LL << 30)) return FSE_EINVAL;
@@ -261,13 +261,6 @@ static int check_frame(const fse_frame &f) {
 // Batch execution on device-resident frames
 // ---------------------------------------------------------------------------
 
-#define CK(call)                                   \
-    do {                                           \
-        if ((call) != cudaSuccess) {               \
-            cudaGetLastError();                    \
-            return FSE_ECUDA;                      \
-        }                                          \
-    } while (0)
 
 // Block-loss map of a host frame: a block is lost when any of its in-image
 // samples is lost (as k_block_loss computes it on the device).
@@ -658,6 +651,9 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
     // The staging buffers of the previous batch on this workspace must have
     // been consumed before they are overwritten.
     if (ws.staged) CK(cudaEventSynchronize(ws.staged));
+    // The previous batch's launches read the device workspace; it may have
+    // been queued on another stream.
+    if (ws.released) CK(cudaStreamWaitEvent(stream, ws.released, 0));
 
     Batch b;
     if ((rc = setup_frames(ctx, ws, frames, n, p, b))) return rc;
@@ -748,6 +744,9 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
         }
     }
 
+    if (!ws.released) CK(cudaEventCreateWithFlags(&ws.released, cudaEventDisableTiming));
+    CK(cudaEventRecord(ws.released, stream));
+
     // ---- what the inspection entry points read back ----
     ws.lost_blocks = b.lost_blocks;
     ws.groups = b.max_groups;
@@ -809,6 +808,8 @@ void fse::release_workspace(fse_ctx *ctx, Workspace &ws) {
     if (ws.side) cudaStreamDestroy(ws.side);
     ws.side = nullptr;
     if (ws.staged) cudaEventDestroy(ws.staged);
+    if (ws.released) cudaEventDestroy(ws.released);
+    ws.released = nullptr;
     for (int k = 0; k < Workspace::kKernelRing; ++k) {
         if (ws.k_begin[k]) cudaEventDestroy(ws.k_begin[k]);
         if (ws.k_end[k]) cudaEventDestroy(ws.k_end[k]);
@@ -865,6 +866,7 @@ extern "C" void fse_ctx_destroy(fse_ctx *ctx) {
     cudaSetDevice(ctx->device);
     stop_server(ctx);
     cudaDeviceSynchronize();
+    release_host_batches(ctx);
     release_workspace(ctx, ctx->ws);
     ctx->dev_release(ctx->tw_dev);
     for (auto &e : ctx->rho_tabs) ctx->dev_release(e.second);
@@ -958,61 +960,6 @@ extern "C" int fse_conceal_batch(fse_ctx *ctx, const fse_frame *frames, int n,
     ctx->last_executor = ctx->ws.executor;
     ctx->last_ctas = ctx->ws.ctas_per_sm;
     return rc;
-}
-
-extern "C" int fse_conceal_batch_host(fse_ctx *ctx, const fse_frame *frames, int n,
-                                      const fse_params *params, void *cuda_stream) {
-    if (!ctx || !frames || n <= 0) return FSE_EINVAL;
-    int rc = check_params(params);
-    if (rc) return rc;
-    for (int i = 0; i < n; ++i)
-        if ((rc = check_frame(frames[i]))) return rc;
-    std::lock_guard<std::mutex> lk(ctx->api_mu);
-    cudaSetDevice(ctx->device);
-    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
-    Workspace &ws = ctx->ws;
-    size_t total = 0;
-    std::vector<size_t> off(n + 1, 0);
-    // device rows are padded to 16 bytes (TMA row pitch)
-    auto pitch = [&](int i) { return (frames[i].width + 15) & ~15; };
-    for (int i = 0; i < n; ++i) {
-        off[i + 1] = off[i] + (((size_t)frames[i].height * pitch(i) + 255) & ~(size_t)255);
-    }
-    total = off[n];
-    rc = ctx->dev_reserve(ws.d_luma, total);
-    if (!rc) rc = ctx->dev_reserve(ws.d_mask, total);
-    if (!rc) rc = ctx->dev_reserve(ws.d_out, total);
-    if (rc) return rc;
-    std::vector<fse_frame> dev(n);
-    for (int i = 0; i < n; ++i) {
-        const fse_frame &h = frames[i];
-        uint8_t *dl = static_cast<uint8_t *>(ws.d_luma.ptr) + off[i];
-        uint8_t *dm = static_cast<uint8_t *>(ws.d_mask.ptr) + off[i];
-        uint8_t *dout = static_cast<uint8_t *>(ws.d_out.ptr) + off[i];
-        CK(cudaMemcpy2DAsync(dl, pitch(i), h.luma, h.stride, h.width, h.height,
-                             cudaMemcpyHostToDevice, stream));
-        CK(cudaMemcpy2DAsync(dm, pitch(i), h.loss_mask, h.stride, h.width, h.height,
-                             cudaMemcpyHostToDevice, stream));
-        dev[i] = fse_frame{dl, dout, dm, h.width, h.height, pitch(i)};
-    }
-    // The block-loss maps come from the host masks, on the worker threads,
-    // while the copies run; planning then needs no device round trip.
-    std::vector<std::vector<uint8_t>> lost(n);
-    ctx->pool.run(n, [&](int i) { lost[i] = host_block_loss(frames[i], params->block); });
-    rc = run_batch(ctx, ws, dev.data(), n, params, stream, &lost);
-    ctx->last_lost_blocks = ws.lost_blocks;
-    ctx->last_groups = ws.groups;
-    ctx->last_launches = ws.launches;
-    ctx->last_executor = ws.executor;
-    ctx->last_ctas = ws.ctas_per_sm;
-    if (rc) return rc;
-    for (int i = 0; i < n; ++i) {
-        const fse_frame &h = frames[i];
-        CK(cudaMemcpy2DAsync(h.out, h.stride, dev[i].out, dev[i].stride, h.width, h.height,
-                             cudaMemcpyDeviceToHost, stream));
-    }
-    CK(cudaStreamSynchronize(stream));
-    return read_status(ctx, ws, stream);
 }
 
 extern "C" int fse_extrapolate_areas(fse_ctx *ctx, const float *area_f,

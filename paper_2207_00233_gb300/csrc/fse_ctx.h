@@ -17,6 +17,16 @@
 
 #include "../../include/fse.h"
 
+// Returns FSE_ECUDA from the calling function when a CUDA call fails (and
+// clears the error).
+#define CK(call)                     \
+    do {                             \
+        if ((call) != cudaSuccess) { \
+            cudaGetLastError();      \
+            return FSE_ECUDA;        \
+        }                            \
+    } while (0)
+
 namespace fse {
 
 struct DevBuf {
@@ -36,6 +46,7 @@ struct Workspace {
     HostBuf stage;                 // pinned staging for uploads / readback
     HostBuf io;                    // pinned staging of serving frames
     cudaEvent_t staged = nullptr;  // uploads from `stage` are complete
+    cudaEvent_t released = nullptr;  // the last batch's launches are complete
     // events around the extrapolation launches of the last kKernelRing
     // batches (ring; k_pos is the next slot, k_count the recorded batches)
     static constexpr int kKernelRing = 64;
@@ -59,6 +70,17 @@ struct Workspace {
     int st_slot = 0;
 };
 
+// One batch of host frames in flight (fse_conceal_batch_host_async): device
+// copies of its frames, the events that order the copy streams around its
+// launch, and its status word.
+struct HostBatch {
+    DevBuf d_luma, d_mask, d_out;
+    cudaEvent_t loaded = nullptr;    // inputs on the device (copy-in stream)
+    cudaEvent_t launched = nullptr;  // extrapolation complete (caller's stream)
+    cudaEvent_t done = nullptr;      // outputs in host memory (copy-out stream)
+    uint64_t ticket = 0;             // 0: free
+};
+
 using Clock = std::chrono::steady_clock;
 
 struct Request {
@@ -80,6 +102,7 @@ struct Slot {
 };
 
 int check_params(const fse_params *p);
+int check_frame(const fse_frame &f);
 
 // Host worker threads of a context, started on first use and kept until the
 // context is destroyed (planning the frames of a batch in parallel without
@@ -137,6 +160,15 @@ struct fse_ctx {
 
     int last_lost_blocks = 0, last_groups = 0, last_launches = 0;
 
+    // batches of host frames (synchronous and asynchronous forms): two in
+    // flight at most, copies on their own streams
+    fse::HostBatch hb[2];
+    int hb_next = 0;                   // slot of the next batch
+    uint64_t hb_ticket = 1;            // next ticket
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    fse::HostBuf hb_status;            // pinned status words, one per slot
+    std::map<uint64_t, int> hb_results;  // finished, not yet waited for
+
     // serving
     std::mutex mu;  // guards everything below and the budget accounting
     std::condition_variable cv, done_cv;
@@ -173,5 +205,6 @@ int run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
               const std::vector<std::vector<uint8_t>> *host_lost, int ctas_per_sm = -1);
 int read_status(fse_ctx *ctx, Workspace &ws, cudaStream_t stream);
 void release_workspace(fse_ctx *ctx, Workspace &ws);
+void release_host_batches(fse_ctx *ctx);
 void stop_server(fse_ctx *ctx);
 }  // namespace fse

@@ -416,3 +416,45 @@ def test_inputs_ready_pipelined_planning(fse, ctx):
     finally:
         ctx.fse_ctx_set_option(fse.FSE_OPT_INPUTS_READY, 0)
         ctx.fse_ctx_set_option(fse.FSE_OPT_SPIN_LIMIT, 1 << 23)
+
+
+def test_host_async_pipeline(fse, ctx):
+    """fse_conceal_batch_host_async: three batches enqueued back to back
+    (the third call waits for the first itself) give the bytes of the
+    synchronous call; each ticket is waited for once; a failed device wait
+    is reported by its own batch's wait and not by the next batch's."""
+    import torch
+    sets = [fse_synth.random_frame(h, w, rate, s) for (h, w, rate, s) in
+            [(96, 160, 0.3, 61), (128, 96, 0.45, 62), (64, 64, 0.6, 63)]]
+    p = _params(fse, 60, 1, "persistent")
+    ref = []
+    for img, mask in sets:
+        out = np.empty_like(img)
+        ctx.fse_conceal_batch_host([(img, mask, out)], p)
+        ref.append(out)
+    pinned = [(torch.from_numpy(i).pin_memory(), torch.from_numpy(m).pin_memory(),
+               torch.zeros(i.shape, dtype=torch.uint8).pin_memory()) for i, m in sets]
+    tickets = [ctx.fse_conceal_batch_host_async([b], p) for b in pinned]
+    assert len(set(tickets)) == 3
+    for t in reversed(tickets):
+        ctx.fse_wait_batch(t)
+    for (_, _, o), r in zip(pinned, ref):
+        assert np.array_equal(o.numpy(), r)
+    with pytest.raises(fse.FseError) as e:
+        ctx.fse_wait_batch(tickets[0])
+    assert e.value.code == 6  # FSE_ENOTFOUND
+    # a dependency that nothing releases, in the first of two batches
+    try:
+        ctx.fse_ctx_set_option(fse.FSE_OPT_SPIN_LIMIT, 2000)
+        ctx.fse_ctx_set_option(fse.FSE_OPT_TEST_STUCK_DEP, 1)
+        t_bad = ctx.fse_conceal_batch_host_async([pinned[0]], p)
+        ctx.fse_ctx_set_option(fse.FSE_OPT_SPIN_LIMIT, 1 << 23)
+        t_ok = ctx.fse_conceal_batch_host_async([pinned[1]], p)
+        ctx.fse_wait_batch(t_ok)
+        with pytest.raises(fse.FseError) as e:
+            ctx.fse_wait_batch(t_bad)
+        assert e.value.code == 4  # FSE_ETIMEDOUT
+        assert np.array_equal(pinned[1][2].numpy(), ref[1])
+    finally:
+        ctx.fse_ctx_set_option(fse.FSE_OPT_SPIN_LIMIT, 1 << 23)
+        ctx.fse_ctx_set_option(fse.FSE_OPT_TEST_STUCK_DEP, 0)
