@@ -16,6 +16,7 @@ data path; the rank times are max-reduced.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import subprocess
@@ -51,7 +52,7 @@ TRAFFIC_BYTES_PER_LAUNCH = 190.454528e6 + 53.233664e6
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--frames", type=int, default=FRAMES)
@@ -77,15 +78,18 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms from before
+    the warm-up; summary() keeps the samples taken inside the window marked
+    by start() and stop() (host clock), all of them if none fell inside."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.t0 = self.t1 = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
 
     def __enter__(self):
@@ -94,11 +98,17 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
+
+    def start(self):
+        self.t0 = datetime.datetime.now()
+
+    def stop(self):
+        self.t1 = datetime.datetime.now()
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -112,24 +122,31 @@ class ClockSampler:
     def summary(self):
         if self.proc is None or not os.path.exists(self.path):
             return None
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
+                sm, mx = float(parts[2]), float(parts[3])
             except ValueError:
                 continue
-            for n, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        if not sm:
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+            except ValueError:
+                ts = None
+            rows.append((ts, sm, mx, parts[6:10]))
+        inside = [r for r in rows
+                  if r[0] is not None and self.t0 and self.t1 and self.t0 <= r[0] <= self.t1]
+        use = inside or rows
+        if not use:
             return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = {n for r in use for n, v in zip(names, r[3]) if v.lower().startswith("active")}
+        return {"sm_mhz": float(np.median([r[1] for r in use])),
+                "sm_max_mhz": float(max(r[2] for r in use)),
+                "reasons": sorted(reasons), "samples": len(use),
+                "inside_timed_region": bool(inside)}
 
 
 def max_over_ranks(value: float, device) -> float:
@@ -454,6 +471,7 @@ def main():
     # timed region, so a step may plan while the previous one still runs
     ctx.fse_ctx_set_option(fse.FSE_OPT_AUTOTUNE, 0 if args.no_autotune else 1)
     ctx.fse_ctx_set_option(fse.FSE_OPT_INPUTS_READY, 1)
+    clocks = ClockSampler(local).__enter__()  # sampling from before the warm-up
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -468,13 +486,15 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clocks:
-        for i in range(args.steps):
-            flush.zero_()
-            ev[i][0].record(stream)
-            step()
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clocks.stop()
+    clocks.__exit__(None, None, None)
     # the kernel's own events of the timed steps (read after the loop, so that
     # no step waits for the previous one)
     kernel_ms = ctx.fse_recent_kernel_ms(args.steps)
