@@ -235,6 +235,30 @@ def test_full_size_batch_sampled_frames(fse, ctx):
     print(st)
 
 
+@pytest.mark.parametrize("executor", EXECS)
+def test_max_iterations(fse, ctx, executor):
+    """K = FSE_MAX_ITERS, the largest K the C-ABI accepts: the (u, dc) list
+    and the selection trace at their largest, against the oracle."""
+    img, mask = fse_synth.random_frame(64, 96, 0.35, 71)
+    p = _params(fse, fse.FSE_MAX_ITERS, 1, executor)
+    *_, st = run_and_compare(ctx, [(img, mask)], p, f"K={fse.FSE_MAX_ITERS}")
+    print(st)
+
+
+def test_uhd_frame(fse, ctx):
+    """The largest frame of the serving mix, 3840x2160 (240 x 135 blocks),
+    15% mixed isolated/burst losses plus a lost block-row slice, one
+    persistent launch, recomputed in full by the oracle."""
+    img = fse_synth.make_image(2160, 3840, 1077)
+    rng = np.random.default_rng(2077)
+    lost = fse_synth.mixed_block_mask(135, 240, 0.15, rng)
+    lost = fse_synth.slice_rows(lost, 1, rng)
+    mask = fse_synth.blocks_to_pixel_mask(lost, 2160, 3840)
+    p = _params(fse, 200, 1, "persistent")
+    *_, st = run_and_compare(ctx, [(img, mask)], p, "3840x2160")
+    print(st)
+
+
 # ---------------------------------------------------------------------------
 # The per-block computation alone (pre-gathered areas)
 # ---------------------------------------------------------------------------
