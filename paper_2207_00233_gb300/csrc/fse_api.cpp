@@ -976,7 +976,7 @@ extern "C" int fse_extrapolate_areas(fse_ctx *ctx, const float *area_f,
     const uint4 *frags = ctx->frag_table(params->precision, &rc);
     if (rc) return rc;
     const KParams kp{params->rho, params->delta, params->gamma, params->iters, frags,
-                     block_log2(params->block)};
+                     block_log2(params->block), nullptr};  // areas are not staged
     CK(launch_areas(area_f, area_cls, n, kp, rho_tab,
                     static_cast<const float2 *>(ctx->tw_dev.ptr), params->precision, g_out,
                     u_out, dc_out, r_out, static_cast<cudaStream_t>(cuda_stream)));
