@@ -245,7 +245,9 @@ int fse_extrapolate_areas(fse_ctx *ctx, const float *area_f,
 /* Serving.  fse_submit queues one request whose luma/out/loss_mask are
  * HOST pointers; they are borrowed until fse_poll reports done.  Requests
  * are admitted into device batches as workspace memory frees up; batches
- * overlap on the device (continuous batching).  Non-blocking.
+ * overlap on the device (continuous batching).  Page-locked buffers are
+ * copied to and from the device directly; pageable ones through staging
+ * buffers of the library.  Non-blocking.
  * Errors: FSE_EINVAL, FSE_EAGAIN (queue full; retry later). */
 int fse_submit(fse_ctx *ctx, const fse_frame *frame, const fse_params *params,
                uint64_t *ticket);

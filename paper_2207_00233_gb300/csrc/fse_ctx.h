@@ -91,6 +91,8 @@ struct Request {
     fse_stats stats{};
     bool done = false;
     size_t io_off = 0;
+    // page-locked caller buffers are copied directly, without staging
+    bool direct_in = false, direct_out = false;
 };
 
 struct Slot {

@@ -40,11 +40,22 @@ size_t frame_bytes(const fse_frame &f) {
 }
 
 
+// Page-locked host memory (allocated or registered by CUDA): copies to and
+// from it run asynchronously without staging.
+bool page_locked(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 void finish(fse_ctx *ctx, Slot &s, int status) {
     const auto now = Clock::now();
     const int nb = (int)s.reqs.size();
     for (Request *r : s.reqs) {
-        if (status == FSE_OK) {
+        if (status == FSE_OK && !r->direct_out) {
             const uint8_t *src = static_cast<const uint8_t *>(s.ws.io.ptr) + r->io_off;
             for (int y = 0; y < r->frame.height; ++y)
                 std::memcpy(r->frame.out + (size_t)y * r->frame.stride,
@@ -79,31 +90,46 @@ int launch_batch(fse_ctx *ctx, Slot &s) {
     uint8_t *io = static_cast<uint8_t *>(ws.io.ptr);
     std::vector<fse_frame> dev(n);
     std::vector<std::vector<uint8_t>> lost(n);
+    for (Request *r : s.reqs) {
+        r->direct_in = page_locked(r->frame.luma) && page_locked(r->frame.loss_mask);
+        r->direct_out = page_locked(r->frame.out);
+    }
+    // staging copies of pageable frames and the block-loss maps, requests in
+    // parallel on the context's worker threads
+    ctx->pool.run(n, [&](int i) {
+        Request *r = s.reqs[i];
+        const fse_frame &h = r->frame;
+        if (!r->direct_in) {
+            uint8_t *pl = io + r->io_off;          // luma, later the result
+            uint8_t *pm = io + total + r->io_off;  // mask
+            for (int y = 0; y < h.height; ++y) {
+                std::memcpy(pl + (size_t)y * h.width, h.luma + (size_t)y * h.stride, h.width);
+                std::memcpy(pm + (size_t)y * h.width, h.loss_mask + (size_t)y * h.stride, h.width);
+            }
+        }
+        lost[i] = host_block_loss(h, r->params.block);
+        int cnt = 0;
+        for (uint8_t v : lost[i]) cnt += v != 0;
+        r->stats.lost_blocks = cnt;
+    });
     for (int i = 0; i < n; ++i) {
         Request *r = s.reqs[i];
         const fse_frame &h = r->frame;
-        uint8_t *pl = io + r->io_off;          // luma, later the result
-        uint8_t *pm = io + total + r->io_off;  // mask
-        for (int y = 0; y < h.height; ++y) {
-            std::memcpy(pl + (size_t)y * h.width, h.luma + (size_t)y * h.stride, h.width);
-            std::memcpy(pm + (size_t)y * h.width, h.loss_mask + (size_t)y * h.stride, h.width);
-        }
-        lost[i] = host_block_loss(h, r->params.block);
+        const uint8_t *sl = r->direct_in ? h.luma : io + r->io_off;
+        const uint8_t *sm = r->direct_in ? h.loss_mask : io + total + r->io_off;
+        const size_t sp = r->direct_in ? (size_t)h.stride : (size_t)h.width;
         uint8_t *dl = static_cast<uint8_t *>(ws.d_luma.ptr) + r->io_off;
         uint8_t *dm = static_cast<uint8_t *>(ws.d_mask.ptr) + r->io_off;
         uint8_t *dout = static_cast<uint8_t *>(ws.d_out.ptr) + r->io_off;
         const int dp = device_pitch(h);
-        if (cudaMemcpy2DAsync(dl, dp, pl, h.width, h.width, h.height, cudaMemcpyHostToDevice,
+        if (cudaMemcpy2DAsync(dl, dp, sl, sp, h.width, h.height, cudaMemcpyHostToDevice,
                               s.stream) != cudaSuccess ||
-            cudaMemcpy2DAsync(dm, dp, pm, h.width, h.width, h.height, cudaMemcpyHostToDevice,
+            cudaMemcpy2DAsync(dm, dp, sm, sp, h.width, h.height, cudaMemcpyHostToDevice,
                               s.stream) != cudaSuccess) {
             cudaGetLastError();
             return FSE_ECUDA;
         }
         dev[i] = fse_frame{dl, dout, dm, h.width, h.height, dp};
-        int cnt = 0;
-        for (uint8_t v : lost[i]) cnt += v != 0;
-        r->stats.lost_blocks = cnt;
     }
     const fse_params p = s.reqs[0]->params;
     rc = run_batch(ctx, ws, dev.data(), n, &p, s.stream, &lost);
@@ -111,9 +137,10 @@ int launch_batch(fse_ctx *ctx, Slot &s) {
     for (int i = 0; i < n; ++i) {
         Request *r = s.reqs[i];
         s.reqs[i]->stats.groups = ws.groups;  // max over the batch
-        if (cudaMemcpy2DAsync(io + r->io_off, r->frame.width, dev[i].out, dev[i].stride,
-                              r->frame.width, r->frame.height, cudaMemcpyDeviceToHost,
-                              s.stream) != cudaSuccess) {
+        uint8_t *dst = r->direct_out ? r->frame.out : io + r->io_off;
+        const size_t dpitch = r->direct_out ? (size_t)r->frame.stride : (size_t)r->frame.width;
+        if (cudaMemcpy2DAsync(dst, dpitch, dev[i].out, dev[i].stride, r->frame.width,
+                              r->frame.height, cudaMemcpyDeviceToHost, s.stream) != cudaSuccess) {
             cudaGetLastError();
             return FSE_ECUDA;
         }

@@ -121,3 +121,34 @@ def test_memory_budget_admission(fse):
         t = ctx.fse_submit(big, bmask, bout, params)
         ctx.fse_drain(60000)
         assert ctx.fse_poll(t).status == 2
+
+
+def test_page_locked_requests(fse):
+    """Requests whose buffers are page-locked are copied without staging;
+    mixed in one batch with pageable ones, every result equals the
+    synchronous call's."""
+    import torch
+    params = fse.make_params(iters=60, order=fse.FSE_ORDER_OPTIMIZED,
+                             executor=fse.FSE_EXEC_PERSISTENT)
+    reqs = _requests(6)
+    with fse.Context(0) as ctx:
+        alone = []
+        for img, mask in reqs:
+            out = np.empty_like(img)
+            ctx.fse_conceal_batch_host([(img, mask, out)], params)
+            alone.append(out)
+        keep, bufs = [], []
+        for i, (img, mask) in enumerate(reqs):
+            if i % 2 == 0:  # page-locked: numpy views of pinned tensors
+                t = [torch.from_numpy(a).pin_memory() for a in (img, mask)]
+                t.append(torch.full(img.shape, 7, dtype=torch.uint8).pin_memory())
+                keep.append(t)
+                bufs.append(tuple(x.numpy() for x in t))
+            else:
+                bufs.append((img, mask, np.full_like(img, 7)))
+        tickets = [ctx.fse_submit(l, m, o, params) for l, m, o in bufs]
+        assert all(t > 0 for t in tickets)
+        ctx.fse_drain(60000)
+        for t, (_, _, o), ref in zip(tickets, bufs, alone):
+            assert ctx.fse_poll(t).status == 0
+            assert np.array_equal(o, ref)
