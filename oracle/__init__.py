@@ -50,13 +50,16 @@ def lib() -> ctypes.CDLL:
         L.oracle_extrapolate_area.argtypes = [
             ctypes.c_int, ctypes.c_int, ctypes.c_int, _f64p, _u8p,
             ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
-            _OptPtr, _OptPtr, _OptPtr, _OptPtr, _OptPtr, _OptPtr, _OptPtr, _OptPtr, _OptPtr]
+            _OptPtr, _OptPtr, _OptPtr, _OptPtr, _OptPtr, _OptPtr, _OptPtr, _OptPtr, _OptPtr,
+            _OptPtr]
         L.oracle_extrapolate_area.restype = ctypes.c_int
         L.oracle_conceal_frame.argtypes = [
             ctypes.c_int, ctypes.c_int, _u8p, _u8p, ctypes.c_int, ctypes.c_int,
             ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
             ctypes.c_int, ctypes.c_int, _f64p, _u8p, _OptPtr, _OptPtr]
         L.oracle_conceal_frame.restype = ctypes.c_int
+        L.oracle_conceal_frame_ex.argtypes = L.oracle_conceal_frame.argtypes + [_OptPtr, _OptPtr]
+        L.oracle_conceal_frame_ex.restype = ctypes.c_int
         L.oracle_max_threads.argtypes = []
         L.oracle_max_threads.restype = ctypes.c_int
         _lib = L
@@ -104,6 +107,7 @@ class AreaResult:
     dc: np.ndarray      # [K] complex coefficient increments
     R: np.ndarray       # [F, F] complex final weighted residual spectrum
     coef: np.ndarray    # [F, F] complex expansion coefficients
+    margin: np.ndarray  # [K] selection margins (see fse_oracle.h)
 
 
 def extrapolate_area(f: np.ndarray, cls: np.ndarray, F: int, K: int, rho: float,
@@ -121,9 +125,11 @@ def extrapolate_area(f: np.ndarray, cls: np.ndarray, F: int, K: int, rho: float,
     dc = np.empty((max(K, 1), 2), np.float64)
     R = np.empty((F, F, 2), np.float64)
     coef = np.empty((F, F, 2), np.float64)
+    margin = np.empty(max(K, 1), np.float64)
     wg = None if want_g is None else np.ascontiguousarray(want_g, dtype=np.uint8)
     rc = lib().oracle_extrapolate_area(M, N, F, f, cls, rho, delta, gamma, K,
-                                       1 if tie_largest else 0, wg, g, w, R0, W, u, dc, R, coef)
+                                       1 if tie_largest else 0, wg, g, w, R0, W, u, dc, R, coef,
+                                       margin)
     if rc:
         raise ValueError(f"oracle_extrapolate_area failed ({rc})")
 
@@ -131,16 +137,20 @@ def extrapolate_area(f: np.ndarray, cls: np.ndarray, F: int, K: int, rho: float,
         return a[..., 0] + 1j * a[..., 1]
 
     return AreaResult(g=g, w=w, R0=cplx(R0), W=cplx(W), u=u[:K].copy(),
-                      dc=cplx(dc[:K]), R=cplx(R), coef=cplx(coef))
+                      dc=cplx(dc[:K]), R=cplx(R), coef=cplx(coef), margin=margin[:K].copy())
 
 
 def conceal_frame(img: np.ndarray, mask: np.ndarray, *, block: int = 16, border: int = 16,
                   dft: int = 64, iters: int = 200, rho: float = 0.7, delta: float = 0.2,
                   gamma: float = 0.5, order: int = ORDER_OPTIMIZED, threads: int = 1,
-                  trace: bool = False):
+                  trace: bool = False, classes: bool = False, margins: bool = False):
     """Conceal one frame.  Returns (work FP64 [H,W], out uint8 [H,W],
     group_of_block int32 [BH,BW]), plus the selection trace
-    [BH*BW, iters] int32 (-2 for blocks without loss) when ``trace``."""
+    [BH*BW, iters] int32 (-2 for blocks without loss) when ``trace``, the
+    sub-area classes of every concealed block's area [BH*BW, M, M] uint8
+    (255 for blocks without loss) when ``classes``, and the selection
+    margins [BH*BW, iters] float64 (inf for blocks without loss) when
+    ``margins``."""
     img = np.ascontiguousarray(img, dtype=np.uint8)
     mask = np.ascontiguousarray(mask, dtype=np.uint8)
     H, Wd = img.shape
@@ -151,11 +161,19 @@ def conceal_frame(img: np.ndarray, mask: np.ndarray, *, block: int = 16, border:
     out = np.empty((H, Wd), np.uint8)
     gob = np.empty((bh, bw), np.int32)
     ut = np.full((bh * bw, max(iters, 1)), -2, np.int32) if trace else None
-    rc = lib().oracle_conceal_frame(H, Wd, img.ravel(), mask.ravel(), block, border, dft,
-                                    iters, rho, delta, gamma, int(order), int(threads),
-                                    work.ravel(), out.ravel(), gob, ut)
+    M = block + 2 * border
+    ct = np.full((bh * bw, M, M), 255, np.uint8) if classes else None
+    mt = np.full((bh * bw, max(iters, 1)), np.inf) if margins else None
+    rc = lib().oracle_conceal_frame_ex(H, Wd, img.ravel(), mask.ravel(), block, border, dft,
+                                       iters, rho, delta, gamma, int(order), int(threads),
+                                       work.ravel(), out.ravel(), gob, ut, ct, mt)
     if rc:
         raise ValueError(f"oracle_conceal_frame failed ({rc})")
+    res = [work, out, gob]
     if trace:
-        return work, out, gob, ut[:, :iters]
-    return work, out, gob
+        res.append(ut[:, :iters])
+    if classes:
+        res.append(ct)
+    if margins:
+        res.append(mt[:, :iters])
+    return tuple(res)

@@ -288,7 +288,7 @@ int oracle_extrapolate_area(int M, int N, int F, const double *f,
                             const uint8_t *want_g, double *g_out,
                             double *w_out, double *R0_out, double *W_out,
                             int32_t *u_out, double *dc_out, double *R_out,
-                            double *coef_out)
+                            double *coef_out, double *margin_out)
 {
     if (M <= 0 || N <= 0 || F <= 0 || M > F || N > F || K < 0 || !f || !cls)
         return -1;
@@ -325,11 +325,16 @@ int oracle_extrapolate_area(int M, int N, int F, const double *f,
     /* W[0] = sum of the weights; every basis function has weighted energy
      * sum w |phi_k|^2 = W[0]. */
     const double W0 = W[0];
+    /* Scale of the selection margins: sum |w f| + W[0] * sum |dc| so far. */
+    double scale = 0.0;
+    for (int i = 0; i < M * N; ++i)
+        scale += fabs(x[i]);
 
     for (int it = 0; it < K; ++it) {
         if (!(W0 > 0.0)) {
             if (u_out) u_out[it] = -1;
             if (dc_out) { dc_out[2 * it] = 0.0; dc_out[2 * it + 1] = 0.0; }
+            if (margin_out) margin_out[it] = HUGE_VAL;
             continue;
         }
         /* Selection: largest decrease of the weighted residual energy,
@@ -343,6 +348,21 @@ int oracle_extrapolate_area(int M, int N, int F, const double *f,
                 u = k;
             }
         }
+        /* Margin of the choice: |R_w[u]| minus the largest magnitude that is
+         * strictly smaller (exact ties are resolved by the index rule), in
+         * units of the scale above.  A small margin is a near-tie that a
+         * lower precision may resolve the other way. */
+        if (margin_out) {
+            double second = -1.0;
+            for (size_t k = 0; k < FF; ++k) {
+                double e = R[2 * k] * R[2 * k] + R[2 * k + 1] * R[2 * k + 1];
+                if (e < best && e > second)
+                    second = e;
+            }
+            margin_out[it] = (second < 0.0 || !(scale > 0.0))
+                                 ? HUGE_VAL
+                                 : (sqrt(best) - sqrt(second)) / scale;
+        }
         /* Orthogonality deficiency compensation: add gamma times the
          * projection coefficient R_w[u] / W[0]. */
         const double dcr = gamma * R[2 * u] / W0;
@@ -351,6 +371,7 @@ int oracle_extrapolate_area(int M, int N, int F, const double *f,
         coef[2 * u + 1] += dci;
         if (u_out) u_out[it] = (int32_t)u;
         if (dc_out) { dc_out[2 * it] = dcr; dc_out[2 * it + 1] = dci; }
+        scale += W0 * sqrt(dcr * dcr + dci * dci);
 
         /* Weighted residual update in the transform domain:
          * R_w[k] -= dc * W[(k - u) mod F] for every k. */
@@ -405,6 +426,18 @@ int oracle_conceal_frame(int H, int Wd, const uint8_t *img,
                          double rho, double delta, double gamma, int order,
                          int threads, double *work, uint8_t *out,
                          int32_t *group_of_block_out, int32_t *u_trace)
+{
+    return oracle_conceal_frame_ex(H, Wd, img, mask, B, d, F, K, rho, delta,
+                                   gamma, order, threads, work, out,
+                                   group_of_block_out, u_trace, NULL, NULL);
+}
+
+int oracle_conceal_frame_ex(int H, int Wd, const uint8_t *img,
+                            const uint8_t *mask, int B, int d, int F, int K,
+                            double rho, double delta, double gamma, int order,
+                            int threads, double *work, uint8_t *out,
+                            int32_t *group_of_block_out, int32_t *u_trace,
+                            uint8_t *cls_trace, double *margin_trace)
 {
     if (H <= 0 || Wd <= 0 || B <= 0 || d < 0 || !img || !mask || !work || !out)
         return -1;
@@ -480,9 +513,12 @@ int oracle_conceal_frame(int H, int Wd, const uint8_t *img,
                     }
                 }
             int32_t *ut = u_trace ? u_trace + (size_t)b * (size_t)K : NULL;
+            double *mt = margin_trace ? margin_trace + (size_t)b * (size_t)K : NULL;
+            if (cls_trace)
+                memcpy(cls_trace + (size_t)b * M * M, cls, (size_t)M * M);
             int r = oracle_extrapolate_area(M, M, F, f, cls, rho, delta, gamma, K,
                                             0, want, gv, NULL, NULL, NULL, ut,
-                                            NULL, NULL, NULL);
+                                            NULL, NULL, NULL, mt);
             if (r)
                 err |= 1;
             /* Insert the model samples of B_i, clamped to the 8-bit range. */

@@ -39,14 +39,17 @@ void oracle_weights(int M, int N, const uint8_t *cls, double rho, double delta,
  * f, cls: [M*N] row-major.  want_g (optional): which g samples to evaluate.
  * Optional outputs (NULL to skip): g_out [M*N] real part of the model,
  * w_out [M*N], R0_out/W_out/R_out/coef_out [F*F complex interleaved],
- * u_out [K] selected linear index F*k_m + k_n, dc_out [K complex]. */
+ * u_out [K] selected linear index F*k_m + k_n, dc_out [K complex],
+ * margin_out [K]: per iteration, |R_w[u]| minus the largest strictly smaller
+ * |R_w[k]|, divided by sum|w f| + W[0] * sum of the earlier |dc| (HUGE_VAL
+ * when there is no competitor or no support). */
 int oracle_extrapolate_area(int M, int N, int F, const double *f,
                             const uint8_t *cls, double rho, double delta,
                             double gamma, int K, int tie_largest,
                             const uint8_t *want_g, double *g_out,
                             double *w_out, double *R0_out, double *W_out,
                             int32_t *u_out, double *dc_out, double *R_out,
-                            double *coef_out);
+                            double *coef_out, double *margin_out);
 
 /* Whole frame.  img, mask: [H*Wd] uint8 (mask 1 = lost sample).  Block size
  * B, border d (area M = B + 2d <= F).  threads: OpenMP threads over the
@@ -59,6 +62,18 @@ int oracle_conceal_frame(int H, int Wd, const uint8_t *img,
                          double rho, double delta, double gamma, int order,
                          int threads, double *work, uint8_t *out,
                          int32_t *group_of_block_out, int32_t *u_trace);
+
+/* As oracle_conceal_frame, plus (optional) cls_trace [bh*bw][M*M]: the
+ * sub-area class of every area sample of each concealed block as its group
+ * saw the frame (ORACLE_CLS_*; rows of other blocks are left untouched), and
+ * margin_trace [bh*bw][K]: the selection margins of each concealed block
+ * (see oracle_extrapolate_area). */
+int oracle_conceal_frame_ex(int H, int Wd, const uint8_t *img,
+                            const uint8_t *mask, int B, int d, int F, int K,
+                            double rho, double delta, double gamma, int order,
+                            int threads, double *work, uint8_t *out,
+                            int32_t *group_of_block_out, int32_t *u_trace,
+                            uint8_t *cls_trace, double *margin_trace);
 
 int oracle_max_threads(void);
 
