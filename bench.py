@@ -45,7 +45,7 @@ SMS = 152
 SMEM_BYTES_PER_CLK = 128
 FP32_LANES = 128
 # DRAM bytes (read + write) of one k_persistent<FP32> launch on this workload,
-# from the ncu capture summarised in profiles/k_persistent_batch16_1080p_K200.md;
+# from the committed ncu capture of this kernel on this workload (profiles/);
 # None while the kernel differs from the captured one
 TRAFFIC_BYTES_PER_LAUNCH = 190.454528e6 + 53.233664e6
 
@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="persistent launch with the occupancy limit of CTAs per SM, untuned "
                          "(profiling: no candidate launches in the warm-up)")
+    ap.add_argument("--loop-microbench", action="store_true",
+                    help="time the iteration loop alone (fse_loop_microbench) for each "
+                         "selection variant and 1..3 CTAs per SM, print one JSON line, exit")
     ap.add_argument("--precision", default="fp32",
                     choices=["fp32", "tf32", "bf16", "fp16", "bf16x3", "tf32x3"],
                     help="projection arithmetic of the main workload (profiling the "
@@ -448,6 +451,36 @@ def serving_run(fse, rates=(50, 200, 1000), seconds=3.0, pool=12):
     return out
 
 
+LOOP_VARIANTS = {0: "two barriers (warp maxima, search in the winning warp)",
+                 1: "one barrier (row maxima reduced during the update)",
+                 2: "one barrier (every warp searches its maximum)"}
+
+
+def loop_microbench(fse, device, iters=K_ITERS, blocks_per_cta=16):
+    """The iteration loop alone (K = 200, 256-thread CTAs, synthetic
+    spectra) for each selection variant at 1, 2 and 3 CTAs per SM: ns and
+    SM clocks (at the maximum clock) per block-iteration per SM, against the
+    256 clocks of the shared-memory floor (32 KiB of W per iteration at 128 B
+    per clock).  Every variant must select the same indices (checksum)."""
+    out = {"iters": iters, "blocks_per_cta": blocks_per_cta, "floor_clk": 256,
+           "variants": LOOP_VARIANTS}
+    sums = set()
+    for v in LOOP_VARIANTS:
+        for c in (1, 2, 3):
+            try:
+                ns, cs = fse.fse_loop_microbench(v, c, iters, blocks_per_cta, device)
+            except fse.FseError as e:
+                out[f"v{v}_c{c}"] = {"error": str(e)}
+                continue
+            out[f"v{v}_c{c}"] = {"ns": ns, "clk_at_2070": ns * 2.070}
+            sums.add((c, cs))
+    by_c = {}
+    for c, cs in sums:
+        by_c.setdefault(c, set()).add(cs)
+    out["same_selections"] = all(len(v) == 1 for v in by_c.values())
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -464,6 +497,10 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     import paper_2207_00233_gb300 as fse
+
+    if args.loop_microbench:
+        print(json.dumps({"loop_microbench": loop_microbench(fse, local)}), flush=True)
+        return
 
     frames = make_workload(args.frames)
     ctx = fse.Context(local)

@@ -172,6 +172,26 @@ int fse_plan_claims(int n_frames, const int32_t *bw, const int32_t *bh,
  * Errors: FSE_EINVAL (NULL output, bad device), FSE_ENOMEM, FSE_ECUDA. */
 int fse_measure_peaks(int device, double *smem_gbs, double *fp32_tflops);
 
+/* Microbenchmark of the iteration loop alone (Sec. 4: K selections and
+ * transform-domain residual updates of a 64x64 spectrum per block; no
+ * gather, projection or synthesis), so that the cost of each loop design
+ * can be measured apart from the rest of the per-block kernel.  Runs
+ * ctas_per_sm x (SM count) CTAs of 256 threads, each extrapolating
+ * blocks_per_cta synthetic spectra for `iters` iterations, twice (the
+ * first as warm-up).  variant: the selection step of the loop, 0 = two
+ * block barriers per iteration (warp maxima, then the search of the
+ * winning warp), 1 = one barrier (row maxima reduced during the update,
+ * one candidate slot per warp), 2 = one barrier (every warp searches its
+ * maximum).  All variants select the same indices.
+ * Outputs: *ns_per_block_iter = kernel time x SMs / (blocks x iters), i.e.
+ * nanoseconds per block-iteration per SM; *checksum = a hash of every
+ * selected index (equal across variants).
+ * Errors: FSE_EINVAL (NULL output, bad device, variant, iters outside
+ * 1..FSE_MAX_ITERS, blocks_per_cta outside 1..4096, or more CTAs per SM
+ * than can be resident), FSE_ENOMEM, FSE_ECUDA. */
+int fse_loop_microbench(int device, int variant, int ctas_per_sm, int iters,
+                        int blocks_per_cta, double *ns_per_block_iter, uint32_t *checksum);
+
 /* Create a context on CUDA device `device`.  mem_budget bounds the device
  * workspace the context may hold (0 = no limit).  The context owns its
  * workspace (FP32 working frames, plans, status words) and a serving
@@ -318,14 +338,20 @@ int fse_copy_trace(fse_ctx *ctx, int frame, int16_t *dst, void *cuda_stream);
  * Scratch: one fixed array of about 8.5 MB in device memory, declared in the
  * library, that every GPU which loads the library holds until the process
  * exits.  No context is needed and the call makes no device or host
- * allocation (host staging is static too).  The first call on a device
- * looks up that device's address of the array, so make it before any
- * stream capture.  Every call shares the array: calls whose GPU work
- * overlaps (other host threads, other streams) race and must be serialised
- * by the caller; host-side staging is serialised internally.
+ * allocation (host staging is static too).  Every call looks up the current
+ * device's address of the array (the first lookup on a device loads the
+ * library's module there), so make the first call before any stream
+ * capture.  Every call shares the array: calls whose GPU work overlaps
+ * (other host threads, other streams) race and must be serialised by the
+ * caller; host-side staging is serialised internally.
  * Stream-ordered on `cuda_stream`; the call synchronises that stream twice
  * (to read the block-loss map and to release its staging) and returns with
  * the extrapolation launches enqueued.
+ * Cost: this is not the fast path.  Areas are gathered with plain loads
+ * (no TMA staging) and every processing-order group is its own launch, so
+ * the line-scan order (one block per group) is bound by launch latency:
+ * about 2,400 serial launches for a 1080p frame with 30% of its blocks lost.
+ * The processing order is planned by the same code as fse_plan_order.
  * Errors: FSE_EINVAL, FSE_ETOOBIG, FSE_ECUDA. */
 int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_params *params,
                               void *cuda_stream);

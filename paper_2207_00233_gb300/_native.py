@@ -25,7 +25,7 @@ EXPORTED = [
     "fse_plan_order", "fse_plan_claims", "fse_ctx_create", "fse_ctx_destroy", "fse_conceal_batch",
     "fse_conceal_batch_host", "fse_conceal_batch_host_async", "fse_wait_batch",
     "fse_extrapolate_areas", "fse_submit", "fse_poll",
-    "fse_drain", "fse_last_batch_info", "fse_last_batch_config", "fse_ctx_set_option", "fse_copy_work", "fse_copy_trace", "fse_last_kernel_ms", "fse_recent_kernel_ms", "fse_conceal_frame_noalloc", "fse_measure_peaks", "fse_strerror",
+    "fse_drain", "fse_last_batch_info", "fse_last_batch_config", "fse_ctx_set_option", "fse_copy_work", "fse_copy_trace", "fse_last_kernel_ms", "fse_recent_kernel_ms", "fse_conceal_frame_noalloc", "fse_measure_peaks", "fse_loop_microbench", "fse_strerror",
 ]
 FSE_OPT_SPIN_LIMIT, FSE_OPT_PERSISTENT_CTAS, FSE_OPT_SERVE_SLOTS = 1, 2, 3
 FSE_OPT_SERVE_MAX_BATCH, FSE_OPT_TEST_STUCK_DEP, FSE_OPT_KEEP_TRACE = 4, 5, 6
@@ -75,6 +75,9 @@ def lib() -> ctypes.CDLL:
     L.fse_plan_claims.argtypes = [cint, vp, vp, vp, cint, cint, cint, vp, vp, ctypes.POINTER(i32)]
     L.fse_measure_peaks.argtypes = [cint, ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double)]
+    L.fse_loop_microbench.argtypes = [cint, cint, cint, cint, cint,
+                                      ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_uint32)]
     L.fse_ctx_create.argtypes = [ctypes.POINTER(vp), cint, ctypes.c_size_t]
     L.fse_ctx_destroy.argtypes = [vp]
     L.fse_ctx_destroy.restype = None
@@ -169,6 +172,17 @@ def fse_measure_peaks(device: int = 0):
     _check(lib().fse_measure_peaks(int(device), ctypes.byref(smem), ctypes.byref(fp32)),
            "fse_measure_peaks")
     return smem.value, fp32.value
+
+
+def fse_loop_microbench(variant: int, ctas_per_sm: int, iters: int = 200,
+                        blocks_per_cta: int = 8, device: int = 0):
+    """Iteration loop alone: (ns per block-iteration per SM, checksum of the
+    selected indices)."""
+    ns, cs = ctypes.c_double(0), ctypes.c_uint32(0)
+    _check(lib().fse_loop_microbench(int(device), int(variant), int(ctas_per_sm), int(iters),
+                                     int(blocks_per_cta), ctypes.byref(ns), ctypes.byref(cs)),
+           "fse_loop_microbench")
+    return ns.value, cs.value
 
 
 def fse_plan_claims(group_maps, block: int = 16, workers: int = 0, mode: int = 0):

@@ -204,4 +204,15 @@ void delay_claims(std::vector<FrameDepths> &frames, int workers, std::vector<int
 void schedule_claims(std::vector<FrameDepths> &frames, int workers, std::vector<int2> &items);
 bool precision_supported(int precision);
 
+// Processing order of one frame (fse_plan.cpp): line scan or Algorithm 1,
+// with the outputs of fse_plan_order, in caller-provided scratch of
+// plan_scratch_bytes(bw, bh) bytes (4-byte aligned; unused for line scan).
+// Allocates nothing.
+constexpr size_t plan_scratch_bytes(int bw, int bh) {
+    return (size_t)(bw + 2) * (bh + 2) * 5 + (size_t)14 * bw * bh * 4 + 14 * 4;
+}
+int plan_order_core(int bw, int bh, const uint8_t *block_lost, int order,
+                    int32_t *group_of_block, int32_t *group_ptr, int32_t *block_ids,
+                    int32_t *n_groups, void *scratch);
+
 }  // namespace fse

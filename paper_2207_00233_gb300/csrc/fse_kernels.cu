@@ -18,7 +18,9 @@
 // in the W4 layout (see fse_internal.h): one 16-byte load per pair.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
+#include <mutex>
 #include <type_traits>
 
 #include "../../include/fse.h"
@@ -1284,13 +1286,25 @@ static cudaError_t with_precision(int precision, F f) {
     }
 }
 
-static bool g_attr_done[6] = {false, false, false, false, false, false};
+// The dynamic shared-memory limit is a per-device (per-context) attribute
+// of each kernel: it is set once per device and precision, under a lock
+// (the serving, host-batch and caller threads all launch); bit d of
+// g_attr_done[precision] records device d.  Devices beyond 63 set it on
+// every launch.
+static std::atomic<uint64_t> g_attr_done[6];
+static std::mutex g_attr_mu;
 
 static cudaError_t ensure_attrs(int precision) {
     if (precision < 0 || precision > 5) return cudaErrorInvalidValue;
-    if (g_attr_done[precision]) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+    if (bit && (g_attr_done[precision].load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    if (bit && (g_attr_done[precision].load(std::memory_order_acquire) & bit)) return cudaSuccess;
     const int max_smem = smem_bytes(FSE_MAX_ITERS);
-    cudaError_t e = with_precision(precision, [&](auto pc) {
+    e = with_precision(precision, [&](auto pc) {
         constexpr int P = decltype(pc)::value;
         cudaError_t r = cudaFuncSetAttribute(k_group<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              max_smem);
@@ -1301,7 +1315,7 @@ static cudaError_t ensure_attrs(int precision) {
         return cudaFuncSetAttribute(k_areas<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     max_smem);
     });
-    if (e == cudaSuccess) g_attr_done[precision] = true;
+    if (e == cudaSuccess && bit) g_attr_done[precision].fetch_or(bit, std::memory_order_release);
     return e;
 }
 

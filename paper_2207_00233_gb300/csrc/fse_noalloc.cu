@@ -46,12 +46,7 @@ constexpr size_t kScratchBytes = align256(kOffWork + (size_t)kNaMaxH * kNaWStrid
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Device address of g_noalloc_scratch per device (the symbol's name is only
-// a host-side stand-in; it is resolved once per device with that device
-// current).
-constexpr int kMaxDevices = 64;
-unsigned char *g_scratch_ptr[kMaxDevices] = {};
-std::mutex g_mu;  // guards the static host staging below and the set-up
+std::mutex g_mu;  // guards the static host staging below
 
 // Static host staging.
 FrameDesc h_desc;
@@ -60,11 +55,11 @@ float h_rho[kArea * kArea];
 int h_lost_off[2];
 uint8_t h_lost[kNaMaxBlocks];
 int32_t h_gob[kNaMaxBlocks];
+int32_t h_ids[kNaMaxBlocks];
+int32_t h_group_ptr[kNaMaxBlocks + 1];
 int2 h_items[kNaMaxBlocks];
-int h_group_start[kNaMaxBlocks + 1];
-// planner state, padded by one block on every side
-int h_n[(kNaMaxBh + 2) * (kNaMaxBw + 2)];
-uint8_t h_in_s[(kNaMaxBh + 2) * (kNaMaxBw + 2)];
+// scratch of the processing-order planner (the one fse_plan_order uses)
+int32_t h_plan_scratch[(plan_scratch_bytes(kNaMaxBw, kNaMaxBh) + 3) / 4];
 
 // cos / sin of 2 pi t / 64 with exact symmetries (t and 64 - t mirror each
 // other; axis values exact).
@@ -94,87 +89,6 @@ void na_twiddles(float2 *tw) {
     for (int t = 0; t < kDft; ++t) tw[t] = make_float2((float)c[t], (float)s[t]);
 }
 
-// Algorithm 1 (Sec. 3) or line scan on the static arrays.  Fills h_gob and
-// h_items (group order, raster order inside a group) and h_group_start.
-int na_plan(int bw, int bh, int order, int *n_groups, int *n_items) {
-    const int nb = bw * bh;
-    if (order == FSE_ORDER_LINESCAN) {
-        int g = 0;
-        for (int b = 0; b < nb; ++b) {
-            if (h_lost[b]) {
-                h_group_start[g] = g;
-                h_items[g] = make_int2(0, b);
-                h_gob[b] = g++;
-            } else {
-                h_gob[b] = -1;
-            }
-        }
-        h_group_start[g] = g;
-        *n_groups = g;
-        *n_items = g;
-        return FSE_OK;
-    }
-    const int pw = bw + 2;
-    auto N = [&](int by, int bx) -> int & { return h_n[(by + 1) * pw + (bx + 1)]; };
-    auto S = [&](int by, int bx) -> uint8_t & { return h_in_s[(by + 1) * pw + (bx + 1)]; };
-    for (int i = 0; i < (bh + 2) * pw; ++i) {
-        h_n[i] = -0x40000000;
-        h_in_s[i] = 0;
-    }
-    int pending = 0;
-    for (int by = 0; by < bh; ++by)
-        for (int bx = 0; bx < bw; ++bx) {
-            const bool rows = by == 0 || by == bh - 1, cols = bx == 0 || bx == bw - 1;
-            N(by, bx) = (rows && cols) ? 5 : (rows || cols) ? 3 : 0;
-        }
-    for (int by = 0; by < bh; ++by)
-        for (int bx = 0; bx < bw; ++bx)
-            if (h_lost[by * bw + bx])
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dx = -1; dx <= 1; ++dx)
-                        if (dy | dx) N(by + dy, bx + dx) += 1;
-    for (int b = 0; b < nb; ++b) {
-        if (!h_lost[b]) {
-            N(b / bw, b % bw) = -1;
-            h_gob[b] = -1;
-        } else {
-            ++pending;
-        }
-    }
-    int g = 0, pos = 0;
-    while (pending > 0) {
-        int nmin = 0x7fffffff;
-        for (int by = 0; by < bh; ++by)
-            for (int bx = 0; bx < bw; ++bx)
-                if (N(by, bx) >= 0 && N(by, bx) < nmin) nmin = N(by, bx);
-        h_group_start[g] = pos;
-        const int first = pos;
-        for (int by = 0; by < bh; ++by)
-            for (int bx = 0; bx < bw; ++bx) {
-                if (N(by, bx) != nmin) continue;
-                if (S(by, bx - 1) | S(by - 1, bx - 1) | S(by - 1, bx) | S(by - 1, bx + 1))
-                    continue;
-                S(by, bx) = 1;
-                h_items[pos++] = make_int2(0, by * bw + bx);
-            }
-        for (int i = first; i < pos; ++i) {
-            const int b = h_items[i].y, by = b / bw, bx = b % bw;
-            h_gob[b] = g;
-            N(by, bx) = -1;
-            S(by, bx) = 0;
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx)
-                    if ((dy | dx) && N(by + dy, bx + dx) >= 0) N(by + dy, bx + dx) -= 1;
-        }
-        pending -= pos - first;
-        ++g;
-    }
-    h_group_start[g] = pos;
-    *n_groups = g;
-    *n_items = pos;
-    return FSE_OK;
-}
-
 #define NA_CK(call)                    \
     do {                               \
         if ((call) != cudaSuccess) {   \
@@ -200,15 +114,13 @@ extern "C" int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_param
     if (frame->width > kNaMaxW || frame->height > kNaMaxH) return FSE_ETOOBIG;
 
     std::lock_guard<std::mutex> lk(g_mu);
-    int dev = 0;
-    NA_CK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return FSE_EINVAL;
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        NA_CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
-    }
-    unsigned char *base = g_scratch_ptr[dev];
+    // The array's name is a host-side stand-in: its address on the current
+    // device is looked up on every call (cheap next to the call's two stream
+    // synchronisations), so it stays right if the device's context has been
+    // reset and the module reloaded elsewhere.
+    void *sym = nullptr;
+    NA_CK(cudaGetSymbolAddress(&sym, g_noalloc_scratch));
+    unsigned char *base = static_cast<unsigned char *>(sym);
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
 
     FrameDesc *d_desc = reinterpret_cast<FrameDesc *>(base + kOffDesc);
@@ -258,9 +170,12 @@ extern "C" int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_param
     NA_CK(cudaMemcpyAsync(h_lost, d_lost, (size_t)bw * bh, cudaMemcpyDeviceToHost, stream));
     NA_CK(cudaStreamSynchronize(stream));
 
-    int n_groups = 0, n_items = 0;
-    rc = na_plan(bw, bh, params->order, &n_groups, &n_items);
+    int32_t n_groups = 0;
+    rc = plan_order_core(bw, bh, h_lost, params->order, h_gob, h_group_ptr, h_ids, &n_groups,
+                         h_plan_scratch);
     if (rc) return rc;
+    const int n_items = h_group_ptr[n_groups];
+    for (int i = 0; i < n_items; ++i) h_items[i] = make_int2(0, h_ids[i]);
     NA_CK(cudaMemcpyAsync(d_gob, h_gob, sizeof(int32_t) * bw * bh, cudaMemcpyHostToDevice,
                           stream));
     if (n_items > 0)
@@ -275,8 +190,7 @@ extern "C" int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_param
     const KParams kp{params->rho, params->delta, params->gamma, params->iters, nullptr,
                      block_log2(kBlock)};
     for (int g = 0; g < n_groups; ++g)
-        NA_CK(launch_group(d_desc, d_items + h_group_start[g],
-                           h_group_start[g + 1] - h_group_start[g], kp, d_rho, d_tw,
-                           FSE_PREC_FP32, stream));
+        NA_CK(launch_group(d_desc, d_items + h_group_ptr[g], h_group_ptr[g + 1] - h_group_ptr[g],
+                           kp, d_rho, d_tw, FSE_PREC_FP32, stream));
     return FSE_OK;
 }

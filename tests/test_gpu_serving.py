@@ -1,13 +1,14 @@
 """Serving through fse_submit / fse_poll: continuous batching of requests of
 different frame sizes and loss patterns; every result is the same alone and
-in the mix, and matches the oracle on a sampled request."""
+in the mix, and sampled requests meet the parity criterion against the
+oracle."""
 import time
 
 import numpy as np
 import pytest
 
 import fse_synth
-from gpu_util import oracle_conceal
+from gpu_util import run_and_compare
 
 pytestmark = pytest.mark.gpu
 
@@ -79,10 +80,15 @@ def test_results_same_alone_and_in_the_mix(fse):
             assert s.latency_ms >= s.queue_ms >= 0
         with pytest.raises(fse.FseError):
             ctx.fse_poll(tickets[0])  # released after completion
-    img, mask = reqs[0]
-    o_work, o_out, _ = oracle_conceal(img, mask, params)
-    lost = mask != 0
-    assert np.abs(outs[0][lost].astype(int) - np.rint(o_work[lost]).astype(int)).max() <= 1
+    # Sampled requests against the oracle with the full parity criterion of
+    # the batch path (sample by sample on clean blocks, validity elsewhere):
+    # the batch path with traces gives the same bytes as the served result.
+    with fse.Context(0) as tctx:
+        tctx.fse_ctx_set_option(fse.FSE_OPT_KEEP_TRACE, 1)
+        for i in (0, 3):
+            dev_outs, _, _, st = run_and_compare(tctx, [reqs[i]], params, f"served request {i}")
+            assert np.array_equal(outs[i], dev_outs[0]), i
+            print(i, st)
 
 
 def test_mixed_parameters_are_batched_separately(fse):

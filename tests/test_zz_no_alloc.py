@@ -4,7 +4,9 @@ budget).  Its scratch is one fixed device array inside the library; the test
 calls it through the C-ABI twice in a row, on two different frames, and
 checks each result against the regular entry point fse_conceal_batch run
 with the same parameters (groups executor, FP32), within the pixel
-tolerance of the parity tests.  It also checks the size limit.
+tolerance of the parity tests, in both processing orders.  It also covers a
+frame concealed in place (out == luma) whose sides are not multiples of 16,
+and the size limit.
 
 Collected last on purpose: a run that stops at the first failure has run
 every other test before this one.
@@ -36,14 +38,21 @@ def _noalloc(fse, luma, mask, out, params, stream):
     return fse.lib().fse_conceal_frame_noalloc(ctypes.byref(fr), ctypes.byref(params), stream)
 
 
-def test_noalloc_matches_regular_entry_point_twice(fse):
+@pytest.mark.parametrize("order", ["optimized", "linescan"])
+def test_noalloc_matches_regular_entry_point_twice(fse, order):
     import torch
     dev = torch.device("cuda:0")
     stream = torch.cuda.current_stream().cuda_stream
-    params = fse.make_params(iters=200, rho=0.7, delta=0.2, gamma=0.5,
-                             order=fse.FSE_ORDER_OPTIMIZED, executor=fse.FSE_EXEC_GROUPS)
-    frames = [fse_synth.workload_mixed_512()[0],            # 512 x 512, mixed losses
-              fse_synth.random_frame(1080, 1920, 0.3, 41)]  # the size limit's frame
+    optimized = order == "optimized"
+    params = fse.make_params(iters=200 if optimized else 60, rho=0.7, delta=0.2, gamma=0.5,
+                             order=fse.FSE_ORDER_OPTIMIZED if optimized else fse.FSE_ORDER_LINESCAN,
+                             executor=fse.FSE_EXEC_GROUPS)
+    if optimized:
+        frames = [fse_synth.workload_mixed_512()[0],            # 512 x 512, mixed losses
+                  fse_synth.random_frame(1080, 1920, 0.3, 41)]  # the size limit's frame
+    else:  # line scan: one launch per lost block, so smaller frames
+        frames = [fse_synth.workload_single_128()[0],
+                  fse_synth.random_frame(200, 264, 0.3, 43)]
     tens = []
     for img, mask in frames:
         luma = torch.from_numpy(img).to(dev)
@@ -63,6 +72,30 @@ def test_noalloc_matches_regular_entry_point_twice(fse):
             assert np.array_equal(a[mask == 0], img[mask == 0])
             assert np.abs(a - b).max() <= 1
             assert (a != b).sum() == 0
+
+
+def test_noalloc_in_place_odd_size(fse):
+    """out == luma (the lost samples are overwritten in place) on a frame of
+    1080 x 1918 samples: partial blocks on the right edge, and a row pitch
+    that is not a multiple of 16."""
+    import torch
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream().cuda_stream
+    params = fse.make_params(iters=100, order=fse.FSE_ORDER_OPTIMIZED,
+                             executor=fse.FSE_EXEC_GROUPS)
+    img, mask = fse_synth.random_frame(1080, 1918, 0.25, 44)
+    buf = torch.from_numpy(img).to(dev)
+    m = torch.from_numpy(mask).to(dev)
+    for _ in range(2):  # the second call conceals an already concealed frame
+        buf.copy_(torch.from_numpy(img))
+        rc = _noalloc(fse, buf, m, buf, params, stream)
+        assert rc == 0, fse.strerror(rc)
+    torch.cuda.synchronize()
+    got = buf.cpu().numpy()
+    ref = np.empty_like(img)
+    with fse.Context(0) as ctx:
+        ctx.fse_conceal_batch_host([(img, mask, ref)], params)
+    assert np.array_equal(got, ref)
 
 
 def test_noalloc_rejects_frames_beyond_its_scratch(fse):
