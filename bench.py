@@ -67,6 +67,10 @@ def parse():
     ap.add_argument("--loop-microbench", action="store_true",
                     help="time the iteration loop alone (fse_loop_microbench) for each "
                          "selection variant and 1..3 CTAs per SM, print one JSON line, exit")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="seconds of arrivals per serving rate (the configuration names 60)")
+    ap.add_argument("--loop-variants", default="", help="comma-separated variants (default all)")
+    ap.add_argument("--loop-ctas", default="", help="comma-separated CTAs per SM (default 1,2,3)")
     ap.add_argument("--precision", default="fp32",
                     choices=["fp32", "tf32", "bf16", "fp16", "bf16x3", "tf32x3"],
                     help="projection arithmetic of the main workload (profiling the "
@@ -175,17 +179,15 @@ def make_workload(frames: int):
 
 def run_reference(args):
     """The FP64 CPU oracle on the host cores: each step conceals a bounded
-    sample of the workload (the top 256 rows = 16 block rows of one frame)."""
+    sample of the workload, one whole 1920x1080 frame of the batch (the same
+    sample unit as the cpu_baseline object of the GPU line)."""
     import oracle
     rank, world, _ = dist_env()
     if rank != 0:
         return
     frames = make_workload(args.frames)
     threads = oracle.max_threads()
-    samples = []
-    for i in range(args.warmup + args.steps):
-        img, mask = frames[i % len(frames)]
-        samples.append((np.ascontiguousarray(img[:256]), np.ascontiguousarray(mask[:256])))
+    samples = [frames[i % len(frames)] for i in range(args.warmup + args.steps)]
     times, blocks = [], 0
     for i, (img, mask) in enumerate(samples):
         t0 = time.perf_counter()
@@ -197,8 +199,9 @@ def run_reference(args):
             blocks += int((gob >= 0).sum())
     total = sum(times)
     value = blocks / total
-    sample = (f"top 256 rows (16 block rows) of one 1920x1080 frame per step, frames "
-              f"0..{args.steps - 1}; {blocks} lost blocks over {args.steps} steps")
+    sample = (f"one whole 1920x1080 frame of the 16-frame batch per step (frames "
+              f"{args.warmup % len(frames)}.. cyclically); {blocks} lost blocks over "
+              f"{args.steps} steps")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
@@ -214,11 +217,68 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(frames):
+TAU_SCALE = 2.0 ** -20  # FP32 selection bound (sum|wf| + W[0] sum|dc|) x 2^-20
+
+
+def _psnr(a, b):
+    mse = float(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2))
+    return float("inf") if mse == 0 else 10 * np.log10(255.0 ** 2 / mse)
+
+
+def parity_summary(mask, work, trace, o_work, o_trace, o_margin, gob, B=16, d=16):
+    """GPU frame against the oracle's: a block is clean when its selection
+    trace equals the oracle's and every earlier-group lost block in its area
+    is clean; a root differs while its inputs are clean (a near-tie that
+    FP32 and FP64 resolve differently).  at_risk counts the blocks whose FP64
+    trajectory has a selection margin within tau; every root should be one.
+    Errors are FP32 working values against the FP64 ones on the 8-bit scale."""
+    bh, bw = gob.shape
+    rad = d // B
+    order = sorted((int(gob[by, bx]), by, bx) for by in range(bh) for bx in range(bw)
+                   if gob[by, bx] >= 0)
+    at_risk = (np.asarray(o_margin) <= TAU_SCALE).any(axis=1).reshape(bh, bw) & (gob >= 0)
+    clean = np.zeros((bh, bw), bool)
+    roots = roots_at_risk = 0
+    g_clean, o_clean = [], []
+    for g, by, bx in order:
+        b = by * bw + bx
+        up = all(clean[ny, nx] for ny in range(max(0, by - rad), min(bh, by + rad + 1))
+                 for nx in range(max(0, bx - rad), min(bw, bx + rad + 1))
+                 if (ny, nx) != (by, bx) and 0 <= gob[ny, nx] < g)
+        if np.array_equal(trace[b], o_trace[b]) and up:
+            clean[by, bx] = True
+            ys, xs = slice(by * B, by * B + B), slice(bx * B, bx * B + B)
+            lm = mask[ys, xs] != 0
+            g_clean.append(work[ys, xs][lm])
+            o_clean.append(o_work[ys, xs][lm])
+        elif up:
+            roots += 1
+            roots_at_risk += bool(at_risk[by, bx])
+    lost = mask != 0
+    gc = np.concatenate(g_clean) if g_clean else np.zeros(0)
+    oc = np.concatenate(o_clean) if o_clean else np.zeros(0)
+    n = len(order)
+    return {"blocks": n, "clean_frac": float(clean.sum()) / max(n, 1), "roots": roots,
+            "roots_at_risk": roots_at_risk, "at_risk": int(at_risk.sum()),
+            "max_abs_clean": float(np.abs(gc - oc).max()) if gc.size else 0.0,
+            "psnr_clean_db": _psnr(gc, oc) if gc.size else None,
+            "max_abs_all": float(np.abs(work[lost] - o_work[lost]).max()) if lost.any() else 0.0,
+            "psnr_all_db": _psnr(work[lost], o_work[lost]) if lost.any() else None,
+            "tolerance": "max |d| <= 0.5 and PSNR >= 50 dB on clean blocks; tau = 2^-20 "
+                         "(sum|wf| + W[0] sum|dc|)"}
+
+
+def cpu_baseline(frames, gpu_frame0=None, sweep_works=None):
     """The oracle as it stands on the host cores, on about 10-30 s of work:
     whole frames until 10 s have passed; then the paper's own scheme on a
     bounded sample (Sec. 4, Fig. 4): one thread in line-scan order against
-    the optimized order with the blocks of each group on T threads."""
+    the optimized order with the blocks of each group on T threads.
+
+    The same leg compares the GPU with these oracle runs: frame 0 of the
+    workload (recomputed once more, untimed, with its selection trace and
+    margins) gives the `parity` object, and the 512x512 frame of the
+    paper-scheme sample gives each projection dtype's error against the FP64
+    oracle (`precision_vs_oracle`)."""
     import oracle
     threads = oracle.max_threads()
     t0 = time.perf_counter()
@@ -234,11 +294,13 @@ def cpu_baseline(frames):
     dt = time.perf_counter() - t0
 
     img, mask = fse_synth.workload_mixed_512()[0]
+    last = {}
 
     def blocks_per_s(order, t):
         t1 = time.perf_counter()
-        _, _, gob = oracle.conceal_frame(img, mask, iters=K_ITERS, order=order, threads=t,
-                                         **PARAMS)
+        work, _, gob = oracle.conceal_frame(img, mask, iters=K_ITERS, order=order, threads=t,
+                                            **PARAMS)
+        last[order] = work
         return int((gob >= 0).sum()) / (time.perf_counter() - t1)
 
     linescan = blocks_per_s(oracle.ORDER_LINESCAN, 1)
@@ -251,17 +313,37 @@ def cpu_baseline(frames):
     scheme["unit"] = UNIT
     scheme["sample"] = "one 512x512 frame, 25% mixed isolated/burst block losses, K=200"
     scheme["paper_gain_8_threads"] = "7.18 (16x16 blocks, mixed losses, 8 Opteron cores)"
-    return {"value": blocks / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{used} whole 1920x1080 frame(s) of the workload, {blocks} lost blocks, "
-                      f"OpenMP over the blocks of each group",
-            "paper_scheme": scheme}
+    out = {"value": blocks / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{used} whole 1920x1080 frame(s) of the workload, {blocks} lost blocks, "
+                     f"OpenMP over the blocks of each group",
+           "paper_scheme": scheme}
+    extra = {}
+    if gpu_frame0 is not None:
+        img0, mask0 = frames[0]
+        o_work, _, gob, o_trace, o_margin = oracle.conceal_frame(
+            img0, mask0, iters=K_ITERS, order=oracle.ORDER_OPTIMIZED, threads=threads,
+            trace=True, margins=True, **PARAMS)
+        work, trace = gpu_frame0
+        par = parity_summary(mask0, work, trace, o_work, o_trace, o_margin, gob)
+        par["sample"] = "frame 0 of the 16-frame batch (1920x1080), the benchmark's launch"
+        extra["parity"] = par
+    if sweep_works is not None and oracle.ORDER_OPTIMIZED in last:
+        ref = last[oracle.ORDER_OPTIMIZED][mask == 1]
+        prec = {}
+        for name, g in sweep_works.items():
+            prec[name] = {"max_abs": float(np.abs(g - ref).max()), "psnr_db": _psnr(g, ref)}
+        prec["sample"] = "512x512, 25% mixed losses, K=200: all concealed samples, FP32 " \
+                         "working values against the FP64 oracle"
+        extra["precision_vs_oracle"] = prec
+    return out, extra
 
 
 def precision_sweep(fse, ctx, dev):
     """The 512x512 mixed-loss workload, K = 200, per projection dtype:
     kernel blocks/s, the difference from the FP32 path and the error against
-    the ground truth (the errors against the FP64 oracle are asserted by the
-    precision tests)."""
+    the ground truth; returns the FP32 working values of the concealed
+    samples per dtype too (compared with the FP64 oracle by the CPU-baseline
+    leg)."""
     import torch
     img, mask = fse_synth.workload_mixed_512()[0]
     lost = mask == 1
@@ -276,6 +358,7 @@ def precision_sweep(fse, ctx, dev):
         return float("inf") if mse == 0 else 10 * np.log10(255.0 ** 2 / mse)
 
     res = {}
+    works = {}
     ref = None
     names = [("fp32", fse.FSE_PREC_FP32), ("tf32", fse.FSE_PREC_TF32),
              ("bf16", fse.FSE_PREC_BF16), ("fp16", fse.FSE_PREC_FP16),
@@ -294,6 +377,7 @@ def precision_sweep(fse, ctx, dev):
         ctx.fse_copy_work(0, work)
         torch.cuda.synchronize()
         g = work.cpu().numpy().astype(np.float64)[lost]
+        works[name] = g
         if ref is None:
             ref = g
         row.update({"max_abs_vs_fp32": float(np.abs(g - ref).max()),
@@ -301,7 +385,7 @@ def precision_sweep(fse, ctx, dev):
                     "psnr_vs_truth_db": psnr(g, gt)})
         res[name] = row
     res["workload"] = "512x512, 25% mixed isolated/burst block losses, K=200 (256 blocks)"
-    return res
+    return res, works
 
 
 def order_comparison(fse, ctx, tens, stream):
@@ -373,20 +457,31 @@ def block_size_sweep(fse, ctx, dev, n_frames=8):
     return res
 
 
-def serving_run(fse, rates=(50, 200, 1000), seconds=3.0, pool=12):
-    """Poisson arrivals of host-memory requests (frame sizes uniform over
-    352x288, 1280x720, 1920x1080, 3840x2160; 5-50% block losses, 20% with
-    full-row slices) through fse_submit / fse_poll."""
+SERVE_RATES = (50, 100, 200, 500, 1000, 2000)
+
+
+def serving_run(fse, rates=SERVE_RATES, seconds=10.0, pool=64, latency_budget_ms=50):
+    """Poisson arrivals of host-memory requests through fse_submit / fse_poll:
+    frame sizes uniform over 352x288, 1280x720, 1920x1080, 3840x2160, 5-50%
+    block losses, 20% with one or two full block-row slices.  Each request of
+    the pool has its own loss mask (its own seeded draw); the image content
+    is one generated frame per format.  Admission is latency-aware
+    (FSE_OPT_SERVE_LATENCY_MS): past saturation requests are refused instead
+    of queueing without bound."""
     import time
     import torch
-    # page-locked request buffers (copied without staging): the inputs, and a
-    # ring of 32 output buffers (pageable ones beyond 32 requests in flight)
-    pinned = [tuple(torch.from_numpy(a).pin_memory() for a in fse_synth.serving_request(i))
-              for i in range(pool)]
-    reqs = [(a.numpy(), b.numpy()) for a, b in pinned]
-    max_px = max(img.size for img, _ in reqs)
-    ring = [torch.empty(max_px, dtype=torch.uint8).pin_memory() for _ in range(32)]
-    free = list(range(len(ring)))
+    images = [torch.from_numpy(fse_synth.serving_image(f, 0)).pin_memory() for f in range(4)]
+    reqs = []
+    for i in range(pool):
+        fmt, mask = fse_synth.serving_mask(i)
+        reqs.append((fmt, images[fmt].numpy(), torch.from_numpy(mask).pin_memory()))
+    # page-locked output buffers per format (copied without staging); the
+    # admission bound keeps the requests in flight below the ring sizes, a
+    # pageable buffer is used beyond them
+    ring_n = 48
+    rings = [[torch.empty(tuple(img.shape), dtype=torch.uint8).pin_memory() for _ in range(ring_n)]
+             for img in images]
+    free = [list(range(ring_n)) for _ in images]
     params = fse.make_params(iters=K_ITERS, order=fse.FSE_ORDER_OPTIMIZED,
                              executor=fse.FSE_EXEC_PERSISTENT, precision=fse.FSE_PREC_FP32,
                              **PARAMS)
@@ -395,68 +490,83 @@ def serving_run(fse, rates=(50, 200, 1000), seconds=3.0, pool=12):
     with fse.Context(0) as ctx:
         ctx.fse_ctx_set_option(fse.FSE_OPT_SERVE_SLOTS, 4)
         ctx.fse_ctx_set_option(fse.FSE_OPT_SERVE_MAX_BATCH, 16)
+        ctx.fse_ctx_set_option(fse.FSE_OPT_SERVE_LATENCY_MS, latency_budget_ms)
         # warm-up (the output buffer is borrowed until the request is done)
-        warm_out = np.empty_like(reqs[0][0])
-        t = ctx.fse_submit(reqs[0][0], reqs[0][1], warm_out, params)
-        ctx.fse_drain(60000)
-        ctx.fse_poll(t)
+        for fmt in range(4):
+            j = next(i for i, r in enumerate(reqs) if r[0] == fmt)
+            warm_out = np.empty(tuple(images[fmt].shape), np.uint8)
+            t = ctx.fse_submit(reqs[j][1], reqs[j][2].numpy(), warm_out, params)
+            ctx.fse_drain(60000)
+            ctx.fse_poll(t)
         for rate in rates:
             pending = {}
-            lat, blocks, refused, sub = [], 0, 0, 0
+            lat, queue, blocks, refused, sub = [], [], 0, 0, 0
             t0 = time.perf_counter()
             next_t = t0
             while True:
                 now = time.perf_counter()
                 if now - t0 >= seconds:
                     break
-                if now >= next_t:
-                    img, mask = reqs[sub % pool]
-                    k = free.pop() if free else None
-                    buf = (ring[k].numpy()[:img.size].reshape(img.shape) if k is not None
-                           else np.empty_like(img))
-                    tk = ctx.fse_submit(img, mask, buf, params)
+                while now >= next_t:  # every arrival that is due
+                    fmt, img, mask = reqs[sub % pool]
+                    k = free[fmt].pop() if free[fmt] else None
+                    buf = rings[fmt][k].numpy() if k is not None else np.empty_like(img)
+                    tk = ctx.fse_submit(img, mask.numpy(), buf, params)
                     if tk < 0:
                         refused += 1
                         if k is not None:
-                            free.append(k)
+                            free[fmt].append(k)
                     else:
-                        pending[tk] = (buf, k)
+                        # the output buffer is borrowed until the request is
+                        # done: keep it referenced (a pageable fallback would
+                        # otherwise be freed while the server writes into it)
+                        pending[tk] = (fmt, k, buf)
                     sub += 1
                     next_t += rng.exponential(1.0 / rate)
                 for tk in list(pending):
                     st = ctx.fse_poll(tk)
                     if st is not None:
                         lat.append(st.latency_ms)
+                        queue.append(st.queue_ms)
                         blocks += st.lost_blocks
-                        if pending[tk][1] is not None:
-                            free.append(pending[tk][1])
-                        del pending[tk]
+                        fmt, k, _ = pending.pop(tk)
+                        if k is not None:
+                            free[fmt].append(k)
                 time.sleep(0.0002)
             ctx.fse_drain(600000)
             t_end = time.perf_counter()
-            for tk in list(pending):
+            for tk, (fmt, k, _) in list(pending.items()):
                 st = ctx.fse_poll(tk)
                 lat.append(st.latency_ms)
+                queue.append(st.queue_ms)
                 blocks += st.lost_blocks
-                if pending[tk][1] is not None:
-                    free.append(pending[tk][1])
+                if k is not None:
+                    free[fmt].append(k)
             lat = np.array(lat)
-            out[str(rate)] = {"submitted": sub, "refused": refused, "completed": int(lat.size),
+            out[str(rate)] = {"offered_per_s": sub / seconds, "submitted": sub,
+                              "refused": refused, "completed": int(lat.size),
                               "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
                               "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
+                              "queue_p99_ms": (float(np.percentile(queue, 99)) if queue else None),
                               "blocks_per_s": blocks / (t_end - t0)}
-    out["setup"] = (f"{seconds:.0f} s of Poisson arrivals per rate (req/s), {pool} distinct "
-                    "requests cycled, 4 device slots, up to 16 requests per batch, K=200, fp32; "
-                    "page-locked inputs and outputs (pageable outputs beyond 32 in flight)")
+    out["setup"] = (f"{seconds:.0f} s of Poisson arrivals per rate (req/s); {pool} requests, "
+                    "each with its own loss mask; 4 device slots, up to 16 requests per batch; "
+                    f"latency-aware admission at {latency_budget_ms} ms (FSE_OPT_SERVE_LATENCY_MS); "
+                    "K=200, fp32; page-locked inputs and outputs")
     return out
 
 
 LOOP_VARIANTS = {0: "two barriers (warp maxima, search in the winning warp)",
                  1: "one barrier (row maxima reduced during the update)",
-                 2: "one barrier (every warp searches its maximum)"}
+                 2: "one barrier (every warp searches its maximum)",
+                 3: "two barriers, winning warp named by the warp maxima, pre-packed step",
+                 4: "as 3, with the winning lane's search by match mask and selection tree",
+                 5: "calibration: update only, fixed index sequence (no selection)",
+                 6: "calibration: update + warp reduction + one barrier, fixed indices"}
 
 
-def loop_microbench(fse, device, iters=K_ITERS, blocks_per_cta=16):
+def loop_microbench(fse, device, iters=K_ITERS, blocks_per_cta=16, variants=None,
+                    ctas=(1, 2, 3)):
     """The iteration loop alone (K = 200, 256-thread CTAs, synthetic
     spectra) for each selection variant at 1, 2 and 3 CTAs per SM: ns and
     SM clocks (at the maximum clock) per block-iteration per SM, against the
@@ -465,15 +575,16 @@ def loop_microbench(fse, device, iters=K_ITERS, blocks_per_cta=16):
     out = {"iters": iters, "blocks_per_cta": blocks_per_cta, "floor_clk": 256,
            "variants": LOOP_VARIANTS}
     sums = set()
-    for v in LOOP_VARIANTS:
-        for c in (1, 2, 3):
+    for v in (variants if variants is not None else LOOP_VARIANTS):
+        for c in ctas:
             try:
                 ns, cs = fse.fse_loop_microbench(v, c, iters, blocks_per_cta, device)
             except fse.FseError as e:
                 out[f"v{v}_c{c}"] = {"error": str(e)}
                 continue
             out[f"v{v}_c{c}"] = {"ns": ns, "clk_at_2070": ns * 2.070}
-            sums.add((c, cs))
+            if v <= 4:  # the selecting forms
+                sums.add((c, cs))
     by_c = {}
     for c, cs in sums:
         by_c.setdefault(c, set()).add(cs)
@@ -499,7 +610,12 @@ def main():
     import paper_2207_00233_gb300 as fse
 
     if args.loop_microbench:
-        print(json.dumps({"loop_microbench": loop_microbench(fse, local)}), flush=True)
+        kw = {}
+        if args.loop_variants:
+            kw["variants"] = [int(x) for x in args.loop_variants.split(",")]
+        if args.loop_ctas:
+            kw["ctas"] = [int(x) for x in args.loop_ctas.split(",")]
+        print(json.dumps({"loop_microbench": loop_microbench(fse, local, **kw)}), flush=True)
         return
 
     frames = make_workload(args.frames)
@@ -645,20 +761,38 @@ def main():
                          "frac": flops / (k_ms / 1e3) / 1e12 / fp32_peak,
                          "derived_peak_tflops": derived_fp32}}
 
-    base = None
+    # ---- the benchmark's launch once more, untimed, with selection traces:
+    # frame 0's FP32 working values and trace for the parity report ----
+    gpu_frame0 = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        base = cpu_baseline(frames)
-    sweep = None
+        ctx.fse_ctx_set_option(fse.FSE_OPT_INPUTS_READY, 0)
+        ctx.fse_ctx_set_option(fse.FSE_OPT_KEEP_TRACE, 1)
+        ctx.fse_conceal_batch(tens, params, stream)
+        h0, w0 = frames[0][0].shape
+        wk = torch.empty((h0, w0), dtype=torch.float32, device=dev)
+        ctx.fse_copy_work(0, wk)
+        nb0 = ((h0 + 15) // 16) * ((w0 + 15) // 16)
+        tr = torch.empty(nb0 * K_ITERS, dtype=torch.int16, device=dev)
+        ctx.fse_copy_trace(0, tr)
+        torch.cuda.synchronize()
+        ctx.fse_ctx_set_option(fse.FSE_OPT_KEEP_TRACE, 0)
+        gpu_frame0 = (wk.cpu().numpy().astype(np.float64),
+                      tr.cpu().numpy().astype(np.int32).reshape(nb0, K_ITERS))
+    sweep = sweep_works = None
     bsweep = None
     orders = None
     if rank == 0 and not args.no_sweep:
         ctx.fse_ctx_set_option(fse.FSE_OPT_INPUTS_READY, 0)
         orders = order_comparison(fse, ctx, tens, stream)
-        sweep = precision_sweep(fse, ctx, dev)
+        sweep, sweep_works = precision_sweep(fse, ctx, dev)
         bsweep = block_size_sweep(fse, ctx, dev)
+    base = None
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base, extra = cpu_baseline(frames, gpu_frame0, sweep_works)
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
-        serving = serving_run(fse)
+        serving = serving_run(fse, seconds=args.serve_seconds)
 
     if rank == 0:
         line = {
@@ -686,21 +820,32 @@ def main():
             "lost_mpixel_per_s": mpixel,
             "roofline": roofline,
             "clocks": clk,
-            "plain_path": None if plain is None else {
-                "value": plain, "unit": UNIT,
-                "what": "same frames, one fse_conceal_batch call per frame, one launch per processing-order group, FP32",
-                "batched_over_plain": value / plain},
         }
         if base is not None:
             line["cpu_baseline"] = base
+        # the sweeps first and the summaries last: a reader of the tail of
+        # the line sees the parity and the batched-over-plain claim
         if orders is not None:
             line["orders"] = orders
-        if sweep is not None:
-            line["precision_sweep"] = sweep
         if bsweep is not None:
             line["block_size_sweep"] = bsweep
+        if sweep is not None:
+            line["precision_sweep"] = sweep
         if serving is not None:
             line["serving"] = serving
+        if "precision_vs_oracle" in extra:
+            line["precision_vs_oracle"] = extra["precision_vs_oracle"]
+        if plain is not None:
+            line["plain_path"] = {
+                "value": plain, "unit": UNIT,
+                "what": "same frames, one fse_conceal_batch call per frame, one launch per "
+                        "processing-order group, FP32",
+                "batched_over_plain": value / plain,
+                "claim": "the >= 5x form is the FP32 batched persistent launch (this line's "
+                         "value), at the accuracy of the parity object: no reduced-precision "
+                         "form is faster (precision_sweep)"}
+        if "parity" in extra:
+            line["parity"] = extra["parity"]
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

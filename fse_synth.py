@@ -186,6 +186,27 @@ def serving_request(index: int):
     return img, blocks_to_pixel_mask(lost, h, w)
 
 
+def serving_image(fmt: int, variant: int):
+    """Content of the serving stream: two images per format."""
+    h, w = SERVING_SIZES[fmt]
+    return make_image(h, w, 5000 + 10 * fmt + variant)
+
+
+def serving_mask(index: int):
+    """Format and loss mask of serving request `index` (the same draws as
+    serving_request): size uniform over four formats, loss rate U(5%, 50%),
+    with probability 0.2 one or two extra full block-row slices."""
+    rng = _rng(2000 + index)
+    fmt = int(rng.integers(0, len(SERVING_SIZES)))
+    h, w = SERVING_SIZES[fmt]
+    bh, bw = block_grid(h, w)
+    rate = rng.uniform(0.05, 0.50)
+    lost = iid_block_mask(bh, bw, rate, rng)
+    if rng.random() < 0.2:
+        lost = slice_rows(lost, int(rng.integers(1, 3)), rng)
+    return fmt, blocks_to_pixel_mask(lost, h, w)
+
+
 def random_frame(height: int, width: int, rate: float, seed: int):
     """Generic seeded frame + i.i.d. block mask for tests of arbitrary size."""
     img = make_image(height, width, 1000 + seed)

@@ -182,7 +182,12 @@ int fse_measure_peaks(int device, double *smem_gbs, double *fp32_tflops);
  * block barriers per iteration (warp maxima, then the search of the
  * winning warp), 1 = one barrier (row maxima reduced during the update,
  * one candidate slot per warp), 2 = one barrier (every warp searches its
- * maximum).  All variants select the same indices.
+ * maximum), 3 = two barriers (the winning warp named from the warp maxima,
+ * which alone searches and publishes the pre-packed update step), 4 = as 3
+ * with the search by a match mask and a selection tree.  All variants
+ * select the same indices.  Two calibration forms make no selection (the
+ * index sequence is a fixed hash of the iteration): 5 = the update alone,
+ * 6 = the update with a warp reduction and one block barrier.
  * Outputs: *ns_per_block_iter = kernel time x SMs / (blocks x iters), i.e.
  * nanoseconds per block-iteration per SM; *checksum = a hash of every
  * selected index (equal across variants).
@@ -393,6 +398,14 @@ int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_params *params,
  *                            device wait of a batch is then reported by a
  *                            later call.  0 (default): the masks are read in
  *                            stream order.
+ *   FSE_OPT_SERVE_LATENCY_MS latency-aware admission of fse_submit: while
+ *                            the oldest request not yet on the GPU has
+ *                            waited longer than this many milliseconds,
+ *                            new requests are refused with FSE_EAGAIN, so
+ *                            past saturation the queueing delay stays near
+ *                            the budget instead of growing without bound.
+ *                            0 (default): admission by queue length and
+ *                            memory only.
  * Errors: FSE_EINVAL for an unknown option or value. */
 #define FSE_OPT_SPIN_LIMIT 1
 #define FSE_OPT_PERSISTENT_CTAS 2
@@ -403,6 +416,7 @@ int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_params *params,
 #define FSE_OPT_GROUP_LAUNCHES 7
 #define FSE_OPT_AUTOTUNE 8
 #define FSE_OPT_INPUTS_READY 9
+#define FSE_OPT_SERVE_LATENCY_MS 10
 int fse_ctx_set_option(fse_ctx *ctx, int option, long long value);
 
 const char *fse_strerror(int status);

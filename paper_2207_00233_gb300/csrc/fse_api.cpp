@@ -1081,6 +1081,12 @@ extern "C" int fse_ctx_set_option(fse_ctx *ctx, int option, long long value) {
         ctx->max_batch = (int)value;
         return FSE_OK;
     }
+    case FSE_OPT_SERVE_LATENCY_MS: {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (value < 0 || value > 3600000) return FSE_EINVAL;
+        ctx->serve_latency_ms = (double)value;
+        return FSE_OK;
+    }
     case FSE_OPT_TEST_STUCK_DEP:
         if (value != 0 && value != 1) return FSE_EINVAL;
         ctx->test_stuck_dep = value != 0;

@@ -180,6 +180,7 @@ struct fse_ctx {
     std::unordered_map<uint64_t, fse::Request *> tickets;
     uint64_t next_ticket = 1;
     size_t max_pending = 1 << 16;
+    double serve_latency_ms = 0.0;  // FSE_OPT_SERVE_LATENCY_MS (0: off)
     int n_slots = 4;
     int max_batch = 32;
     std::vector<fse::Slot> slots;

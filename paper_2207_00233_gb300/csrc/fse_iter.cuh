@@ -160,6 +160,116 @@ __device__ __forceinline__ void select_two_barriers(float tmx, const u64 (&rre)[
     uim = cw.z;
 }
 
+// ---- selection: two block barriers, the winning warp named by its maximum -----
+//
+// Warp maxima -> barrier -> every warp reads the eight maxima and names the
+// winning warp: the smallest warp holding the block maximum (warp w owns the
+// indices [512 w, 512 w + 512), so the smallest index lies there).  Only
+// that warp searches; its lane with the smallest index computes
+// dc = gamma R_w[u] / W[0], writes the coefficient list entry and publishes
+// everything the update needs, pre-packed, in one 32-byte slot:
+// (-dc_r, -dc_r, dc_i, dc_i), (-dc_i, -dc_i, u_m << 10, u_n << 4) -> barrier
+// -> every thread loads the slot.
+struct Step {
+    u64 ndcr2, dci2, ndci2;  // packed update constants
+    uint32_t rowoff, coloff; // u_m * 1024, u_n * 16 (W4 byte offsets)
+};
+
+// The thread's smallest slot s (= 2 r for column l, 2 r + 1 for l + 32) whose
+// energy equals estar, found with a match mask and a selection tree; kk is
+// its linear index (all ones if no slot matches).
+__device__ __forceinline__ void search_tree(uint32_t estar, const u64 (&rre)[8],
+                                            const u64 (&rim)[8], uint32_t &kk, float &cre,
+                                            float &cim) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    uint32_t m[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const float2 e = unpack2(energy2(rre[r], rim[r]));
+        m[r] = (__float_as_uint(e.x) == estar ? 1u : 0u) | (__float_as_uint(e.y) == estar ? 2u : 0u);
+    }
+    const uint32_t mask = ((m[0] | (m[1] << 2)) | ((m[2] << 4) | (m[3] << 6))) |
+                          (((m[4] << 8) | (m[5] << 10)) | ((m[6] << 12) | (m[7] << 14)));
+    const int sl = __ffs(mask) - 1;
+    const bool b1 = (sl >> 1) & 1, b2 = (sl >> 2) & 1, b3 = (sl >> 3) & 1;
+    const u64 a0 = b1 ? rre[1] : rre[0], a1 = b1 ? rre[3] : rre[2];
+    const u64 a2 = b1 ? rre[5] : rre[4], a3 = b1 ? rre[7] : rre[6];
+    const u64 c0 = b1 ? rim[1] : rim[0], c1 = b1 ? rim[3] : rim[2];
+    const u64 c2 = b1 ? rim[5] : rim[4], c3 = b1 ? rim[7] : rim[6];
+    const u64 ar = b3 ? (b2 ? a3 : a2) : (b2 ? a1 : a0);
+    const u64 ci = b3 ? (b2 ? c3 : c2) : (b2 ? c1 : c0);
+    const float2 re = unpack2(ar), im = unpack2(ci);
+    const bool hi = sl & 1;
+    cre = hi ? re.y : re.x;
+    cim = hi ? im.y : im.x;
+    kk = mask ? (uint32_t)((8 * w + (sl >> 1)) * kDft + l + (hi ? 32 : 0)) : 0xffffffffu;
+}
+
+template <bool kTree>
+__device__ __forceinline__ void select_named_warp(float tmx, const u64 (&rre)[8],
+                                                  const u64 (&rim)[8], float gw, int it,
+                                                  uint32_t *smax, uint4 *slot, float2 *dcl,
+                                                  uint16_t *ul, Step &st) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const uint32_t wmx = __reduce_max_sync(0xffffffffu, __float_as_uint(tmx));
+    if (l == 0) smax[w] = wmx;
+    __syncthreads();
+    const uint32_t v = smax[l & (kWarps - 1)];
+    const uint32_t estar = __reduce_max_sync(0xffffffffu, v);
+    const int wstar = __ffs(__ballot_sync(0xffffffffu, v == estar) & ((1u << kWarps) - 1u)) - 1;
+    if (w == wstar) {  // warp-uniform
+        uint32_t kk = 0xffffffffu;
+        float cre = 0.f, cim = 0.f;
+        if (__float_as_uint(tmx) == estar) {
+            if (kTree) {
+                search_tree(estar, rre, rim, kk, cre, cim);
+            } else {
+#pragma unroll
+                for (int r = 7; r >= 0; --r) {
+                    const float2 e = unpack2(energy2(rre[r], rim[r]));
+                    const float2 re = unpack2(rre[r]), im = unpack2(rim[r]);
+                    if (__float_as_uint(e.y) == estar) {
+                        kk = (uint32_t)((8 * w + r) * kDft + l + 32);
+                        cre = re.y;
+                        cim = im.y;
+                    }
+                    if (__float_as_uint(e.x) == estar) {
+                        kk = (uint32_t)((8 * w + r) * kDft + l);
+                        cre = re.x;
+                        cim = im.x;
+                    }
+                }
+            }
+        }
+        const uint32_t wk = __reduce_min_sync(0xffffffffu, kk);
+        if (kk == wk) {
+            const float dcr = cre * gw, dci = cim * gw;
+            dcl[it] = make_float2(dcr, dci);
+            ul[it] = (uint16_t)wk;
+            slot[0] = make_uint4(__float_as_uint(-dcr), __float_as_uint(-dcr),
+                                 __float_as_uint(dci), __float_as_uint(dci));
+            slot[1] = make_uint4(__float_as_uint(-dci), __float_as_uint(-dci), (wk >> 6) << 10,
+                                 (wk & 63) << 4);
+        }
+    }
+    __syncthreads();
+    u64 a0, a1, b0, b1;
+    lds_pair(smem_addr(slot), a0, a1);
+    lds_pair(smem_addr(slot + 1), b0, b1);
+    st.ndcr2 = a0;
+    st.dci2 = a1;
+    st.ndci2 = b0;
+    st.rowoff = (uint32_t)b1;
+    st.coloff = (uint32_t)(b1 >> 32);
+}
+
+// Shared address of W4[(8w - u_m) mod 64][(l - u_n) mod 64] from the
+// published offsets; w8k = 8w * 1024, l16 = 16 l.
+__device__ __forceinline__ uint32_t w4_addr_of(uint32_t w4addr, uint32_t w8k, uint32_t l16,
+                                               const Step &st) {
+    return w4addr + ((w8k - st.rowoff) & 0xFC00u) + ((l16 - st.coloff) & 0x3F0u);
+}
+
 // ---- selection: one block barrier, row maxima reduced during the update ------
 //
 // Every row of the thread's entries is reduced over the warp as soon as it

@@ -25,6 +25,7 @@ using namespace fse;
 using namespace fse::iter;
 
 constexpr int kLbSlotOff = kW4Bytes;                  // 2 x 8 uint4: one-barrier slots
+                                                      // (variant 3: the first two)
 constexpr int kLbSmaxOff = kLbSlotOff + 2 * kWarps * 16;  // 8 words: warp maxima
 constexpr int kLbCandOff = kLbSmaxOff + kWarps * 4;   // 8 float4: two-barrier candidates
 constexpr int kLbAOff = kLbCandOff + kWarps * 16;     // 64 float2: 1-D DFT of a
@@ -90,6 +91,50 @@ k_loop(int iters, int blocks, float gamma, uint32_t *sums) {
             rre[r] = pack2((h & 0xffff) * (1.f / 655.36f), (h >> 16) * (1.f / 655.36f));
             rim[r] = pack2((g & 0xffff) * (1.f / 655.36f) - 50.f, (g >> 16) * (1.f / 655.36f) - 50.f);
         }
+        if (V == 5 || V == 6) {
+            // Calibration forms, not FSE: the index sequence is fixed
+            // (u = hash of the iteration), so no selection is made; variant 6
+            // adds the warp reduction and one block barrier per iteration.
+            u64 ndcr2 = 0ull, dci2 = 0ull, ndci2 = 0ull;
+            uint32_t wbase = w4_base(w4addr, 0, 0);
+            uint32_t acc = 0;
+            for (int it = 0; it < iters; ++it) {
+                const float tmx = update_and_max(wbase, ndcr2, dci2, ndci2, rre, rim);
+                uint32_t v = __float_as_uint(tmx);
+                if (V == 6) {
+                    v = __reduce_max_sync(0xffffffffu, v);
+                    if ((tid & 31) == 0) smax[tid >> 5] = v;
+                    __syncthreads();
+                    v = __reduce_max_sync(0xffffffffu, smax[tid & 7]);
+                }
+                acc += v;
+                // (v >> 31 is 0: energies are not negative; it makes the next
+                // iteration depend on this one's update, as a selection does)
+                const uint32_t u = ((it * 2654435761u + b * 40503u) >> 20 ^ (v >> 31)) & 4095u;
+                const float dcr = 1e-3f * (float)(u & 15), dci = -1e-3f * (float)(u >> 8);
+                ndcr2 = pack2(-dcr, -dcr);
+                dci2 = pack2(dci, dci);
+                ndci2 = pack2(-dci, -dci);
+                wbase = w4_base(w4addr, (int)(u >> 6), (int)(u & 63));
+                if (V == 6) __syncthreads();  // smax is rewritten next iteration
+            }
+            if (tid == 0) sum += acc;
+            continue;
+        }
+        if (V == 3 || V == 4) {
+            const uint32_t w8k = (uint32_t)(8 * (tid >> 5)) << 10, l16 = (uint32_t)(tid & 31) << 4;
+            Step st{0ull, 0ull, 0ull, 0u, 0u};  // first pass: dc = 0
+            for (int it = 0; it < iters; ++it) {
+                const uint32_t wb = w4_addr_of(w4addr, w8k, l16, st);
+                const float tmx = update_and_max(wb, st.ndcr2, st.dci2, st.ndci2, rre, rim);
+                select_named_warp<V == 4>(tmx, rre, rim, gw, it, smax, slots, dcl, ul, st);
+                if (tid == 0) sum = sum * 1000003u + ul[it];
+            }
+            __syncthreads();
+            if (tid == 0) sum += ul[iters - 1];
+            __syncthreads();
+            continue;
+        }
         u64 ndcr2 = 0ull, dci2 = 0ull, ndci2 = 0ull;
         uint32_t wbase = w4_base(w4addr, 0, 0);
         for (int it = 0; it < iters; ++it) {
@@ -144,7 +189,7 @@ cudaError_t prepare(int smem, int ctas, int *fit) {
 extern "C" int fse_loop_microbench(int device, int variant, int ctas_per_sm, int iters,
                                    int blocks_per_cta, double *ns_per_block_iter,
                                    uint32_t *checksum) {
-    if (!ns_per_block_iter || !checksum || variant < 0 || variant > 2 || ctas_per_sm < 1 ||
+    if (!ns_per_block_iter || !checksum || variant < 0 || variant > 6 || ctas_per_sm < 1 ||
         iters < 1 || iters > FSE_MAX_ITERS || blocks_per_cta < 1 || blocks_per_cta > 4096)
         return FSE_EINVAL;
     int ndev = 0;
@@ -166,7 +211,11 @@ extern "C" int fse_loop_microbench(int device, int variant, int ctas_per_sm, int
     int fit = 0;
     cudaError_t e = variant == 0   ? prepare<0>(smem, ctas_per_sm, &fit)
                     : variant == 1 ? prepare<1>(smem, ctas_per_sm, &fit)
-                                   : prepare<2>(smem, ctas_per_sm, &fit);
+                    : variant == 2 ? prepare<2>(smem, ctas_per_sm, &fit)
+                    : variant == 3 ? prepare<3>(smem, ctas_per_sm, &fit)
+                    : variant == 4 ? prepare<4>(smem, ctas_per_sm, &fit)
+                    : variant == 5 ? prepare<5>(smem, ctas_per_sm, &fit)
+                                   : prepare<6>(smem, ctas_per_sm, &fit);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return FSE_ECUDA;
@@ -183,8 +232,16 @@ extern "C" int fse_loop_microbench(int device, int variant, int ctas_per_sm, int
             k_loop<0><<<grid, kThreads, smem>>>(iters, blocks_per_cta, 0.5f, sums);
         else if (variant == 1)
             k_loop<1><<<grid, kThreads, smem>>>(iters, blocks_per_cta, 0.5f, sums);
-        else
+        else if (variant == 2)
             k_loop<2><<<grid, kThreads, smem>>>(iters, blocks_per_cta, 0.5f, sums);
+        else if (variant == 3)
+            k_loop<3><<<grid, kThreads, smem>>>(iters, blocks_per_cta, 0.5f, sums);
+        else if (variant == 4)
+            k_loop<4><<<grid, kThreads, smem>>>(iters, blocks_per_cta, 0.5f, sums);
+        else if (variant == 5)
+            k_loop<5><<<grid, kThreads, smem>>>(iters, blocks_per_cta, 0.5f, sums);
+        else
+            k_loop<6><<<grid, kThreads, smem>>>(iters, blocks_per_cta, 0.5f, sums);
     };
     cudaEvent_t a = nullptr, b = nullptr;
     int rc = FSE_OK;

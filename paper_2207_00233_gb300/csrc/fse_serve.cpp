@@ -1,5 +1,10 @@
 // Serving: fse_submit / fse_poll with continuous batching.
 //
+// Admission: a request is refused (FSE_EAGAIN) when the queue is full, or,
+// with FSE_OPT_SERVE_LATENCY_MS, while the oldest queued request has waited
+// longer than the latency budget; a batch is admitted onto a slot when its
+// workspace fits the memory budget.
+//
 // A server thread owns `n_slots` CUDA streams, each with its own workspace.
 // Pending requests (FIFO) are admitted into a batch on a free slot when the
 // workspace for the batch fits the context's memory budget; requests that
@@ -305,12 +310,19 @@ extern "C" int fse_submit(fse_ctx *ctx, const fse_frame *frame, const fse_params
     if (ctx->stop) return FSE_EINVAL;
     if ((rc = start_server(ctx))) return rc;
     if (ctx->pending.size() >= ctx->max_pending) return FSE_EAGAIN;
+    const auto now = Clock::now();
+    // Latency-aware admission: the head of the queue is the oldest request
+    // not yet on the GPU; its wait is the queueing delay a new request would
+    // at least see.
+    if (ctx->serve_latency_ms > 0.0 && !ctx->pending.empty() &&
+        ms_between(ctx->pending.front()->t_submit, now) > ctx->serve_latency_ms)
+        return FSE_EAGAIN;
     Request *r = new (std::nothrow) Request();
     if (!r) return FSE_ENOMEM;
     r->ticket = ctx->next_ticket++;
     r->frame = *frame;
     r->params = *params;
-    r->t_submit = Clock::now();
+    r->t_submit = now;
     ctx->pending.push_back(r);
     ctx->tickets[r->ticket] = r;
     ctx->outstanding += 1;

@@ -158,3 +158,49 @@ def test_page_locked_requests(fse):
         for t, (_, _, o), ref in zip(tickets, bufs, alone):
             assert ctx.fse_poll(t).status == 0
             assert np.array_equal(o, ref)
+
+
+def _offered_load(fse, ctx, params, reqs, seconds, interval_s):
+    """Submit `reqs` cyclically every interval_s for `seconds`; returns
+    (refused, [stats of completed requests])."""
+    outs = [np.empty_like(img) for img, _ in reqs]
+    tickets, refused = [], 0
+    t0 = time.perf_counter()
+    i = 0
+    while time.perf_counter() - t0 < seconds:
+        img, mask = reqs[i % len(reqs)]
+        # each in-flight request needs its own output buffer
+        out = outs[i % len(reqs)] if i < len(reqs) else np.empty_like(img)
+        t = ctx.fse_submit(img, mask, out, params)
+        if t < 0:
+            refused += 1
+        else:
+            tickets.append((t, out))
+        i += 1
+        time.sleep(interval_s)
+    ctx.fse_drain(120000)
+    return refused, [ctx.fse_poll(t) for t, _ in tickets]
+
+
+def test_latency_aware_admission(fse):
+    """Offered load far above what the GPU sustains: without a latency
+    budget every request is queued and the queueing delay grows with the
+    backlog; with FSE_OPT_SERVE_LATENCY_MS = 20 requests are refused while
+    the oldest queued one has waited longer than 20 ms, so the delays of the
+    admitted requests stay bounded."""
+    params = fse.make_params(iters=200, order=fse.FSE_ORDER_OPTIMIZED,
+                             executor=fse.FSE_EXEC_PERSISTENT)
+    reqs = [fse_synth.random_frame(1080, 1920, 0.5, 800 + i) for i in range(4)]
+    res = {}
+    for budget in (0, 20):
+        with fse.Context(0) as ctx:
+            ctx.fse_ctx_set_option(fse.FSE_OPT_SERVE_LATENCY_MS, budget)
+            refused, stats = _offered_load(fse, ctx, params, reqs, 0.6, 0.0005)
+        assert all(s is not None and s.status == 0 for s in stats)
+        q = np.array([s.queue_ms for s in stats])
+        res[budget] = (refused, len(stats), float(np.percentile(q, 90)), float(q.max()))
+    print(res)
+    assert res[0][0] == 0            # no budget: nothing refused ...
+    assert res[20][0] > 0            # ... with a budget, the overload is refused
+    assert res[20][2] < res[0][2]    # and the queueing delay is shorter
+    assert res[20][3] <= 20.0 + 1000.0 * 0.6 / 4  # bounded: far below the unbounded backlog
