@@ -406,6 +406,16 @@ int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_params *params,
  *                            the budget instead of growing without bound.
  *                            0 (default): admission by queue length and
  *                            memory only.
+ *   FSE_OPT_W_TABLES         1 (default): blocks whose sub-area classes are
+ *                            fixed by their eight neighbours (16x16 blocks
+ *                            lost as a whole, FP32 projection) take the
+ *                            spectrum of their weights, W, from a table per
+ *                            class pattern, computed once per context and
+ *                            (rho, delta) and kept in device memory within
+ *                            the memory budget (72,704 bytes per pattern);
+ *                            the block kernels then project only w f.
+ *                            The tables equal what the blocks compute.
+ *                            0: every block computes W.
  * Errors: FSE_EINVAL for an unknown option or value. */
 #define FSE_OPT_SPIN_LIMIT 1
 #define FSE_OPT_PERSISTENT_CTAS 2
@@ -417,6 +427,7 @@ int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_params *params,
 #define FSE_OPT_AUTOTUNE 8
 #define FSE_OPT_INPUTS_READY 9
 #define FSE_OPT_SERVE_LATENCY_MS 10
+#define FSE_OPT_W_TABLES 11
 int fse_ctx_set_option(fse_ctx *ctx, int option, long long value);
 
 const char *fse_strerror(int status);

@@ -30,7 +30,7 @@ EXPORTED = [
 FSE_OPT_SPIN_LIMIT, FSE_OPT_PERSISTENT_CTAS, FSE_OPT_SERVE_SLOTS = 1, 2, 3
 FSE_OPT_SERVE_MAX_BATCH, FSE_OPT_TEST_STUCK_DEP, FSE_OPT_KEEP_TRACE = 4, 5, 6
 FSE_OPT_GROUP_LAUNCHES, FSE_OPT_AUTOTUNE, FSE_OPT_INPUTS_READY = 7, 8, 9
-FSE_OPT_SERVE_LATENCY_MS = 10
+FSE_OPT_SERVE_LATENCY_MS, FSE_OPT_W_TABLES = 10, 11
 
 
 class fse_params(ctypes.Structure):

@@ -267,12 +267,13 @@ int fse::check_frame(const fse_frame &f) {
 std::vector<uint8_t> fse::host_block_loss(const fse_frame &f, int B) {
     const int bh = (f.height + B - 1) / B, bw = (f.width + B - 1) / B;
     std::vector<uint8_t> lost((size_t)bh * bw, 0);
-    // OR the B rows of a block row together 8 bytes at a time, then test
-    // each block's B bytes of the result.
+    // OR (any lost) and AND of "lost" (all lost) of the B rows of a block
+    // row, 8 bytes at a time; then each block's B bytes of the results.
     const size_t words = ((size_t)f.width + 7) / 8;
-    std::vector<uint64_t> acc(words);
+    std::vector<uint64_t> acc(words), all(words);
     for (int by = 0; by < bh; ++by) {
         std::fill(acc.begin(), acc.end(), 0ull);
+        std::fill(all.begin(), all.end(), ~0ull);
         const int y1 = std::min(f.height, (by + 1) * B);
         for (int y = by * B; y < y1; ++y) {
             const uint8_t *row = f.loss_mask + (size_t)y * f.stride;
@@ -281,16 +282,29 @@ std::vector<uint8_t> fse::host_block_loss(const fse_frame &f, int B) {
                 uint64_t v;
                 std::memcpy(&v, row + 8 * k, 8);
                 acc[k] |= v;
+                // bytes of v that are non-zero, as 0x01 per byte
+                uint64_t nz = v | (v >> 4);
+                nz |= nz >> 2;
+                nz |= nz >> 1;
+                all[k] &= nz & 0x0101010101010101ull;
             }
-            uint8_t *bytes = reinterpret_cast<uint8_t *>(acc.data());
-            for (int x = (int)(full * 8); x < f.width; ++x) bytes[x] |= row[x];
+            uint8_t *a = reinterpret_cast<uint8_t *>(acc.data());
+            uint8_t *l = reinterpret_cast<uint8_t *>(all.data());
+            for (int x = (int)(full * 8); x < f.width; ++x) {
+                a[x] |= row[x];
+                l[x] &= row[x] != 0 ? 1 : 0;
+            }
         }
-        const uint8_t *bytes = reinterpret_cast<const uint8_t *>(acc.data());
+        const uint8_t *a = reinterpret_cast<const uint8_t *>(acc.data());
+        const uint8_t *l = reinterpret_cast<const uint8_t *>(all.data());
         for (int bx = 0; bx < bw; ++bx) {
             const int x0 = bx * B, x1 = std::min(f.width, x0 + B);
-            uint8_t any = 0;
-            for (int x = x0; x < x1; ++x) any |= bytes[x];
-            lost[(size_t)by * bw + bx] = any != 0;
+            uint8_t any = 0, every = 1;
+            for (int x = x0; x < x1; ++x) {
+                any |= a[x];
+                every &= l[x] & 1;
+            }
+            lost[(size_t)by * bw + bx] = any ? (every ? kLostWhole : kLostPart) : 0;
         }
     }
     return lost;
@@ -411,7 +425,55 @@ struct Batch {
     std::vector<int2> items;       // claim or launch order
     std::vector<int> level_start;  // launch boundaries (groups executor)
     bool map_kernel = false;       // the loss maps were built on the device
+    std::vector<int32_t> wkey;     // W-table key of each block, -1: none
+    std::vector<uint64_t> wptr;    // address of each block's W table, 0: none
+    bool tables = false;           // some block uses a table
 };
+
+// Whether the blocks of a batch with these parameters can use W tables:
+// 16x16 blocks, FP32 projection, tables on.
+bool wtables_apply(const fse_ctx *ctx, const fse_params *p) {
+    return ctx->w_tables != 0 && p->block == kBlock && p->precision == FSE_PREC_FP32;
+}
+
+// The W-table key of every lost block of frame i (see fse_internal.h):
+// the block lost as a whole and inside the image, each of its 8 neighbours
+// inside the image and not lost, or lost as a whole, or wholly outside.
+void frame_wkeys(const FrameDesc &d, const uint8_t *lost, const int32_t *gob, int32_t *key) {
+    static const int kDy[8] = {-1, -1, -1, 0, 0, 1, 1, 1};
+    static const int kDx[8] = {-1, 0, 1, -1, 1, -1, 0, 1};
+    auto inside = [&](int by, int bx) {
+        return (by + 1) * kBlock <= d.H && (bx + 1) * kBlock <= d.W;
+    };
+    for (int by = 0; by < d.bh; ++by)
+        for (int bx = 0; bx < d.bw; ++bx) {
+            const int b = by * d.bw + bx;
+            key[b] = -1;
+            if (lost[b] != kLostWhole || !inside(by, bx)) continue;
+            int k = 0;
+            bool ok = true;
+            for (int j = 0; j < 8 && ok; ++j) {
+                const int ny = by + kDy[j], nx = bx + kDx[j];
+                int st;
+                if (ny < 0 || ny >= d.bh || nx < 0 || nx >= d.bw) {
+                    st = 3;  // no sample of the cell is in the image
+                } else if (!inside(ny, nx)) {
+                    ok = false;  // a cell cut by the image border
+                    break;
+                } else {
+                    const int c = ny * d.bw + nx;
+                    if (lost[c] == 0) st = 0;
+                    else if (lost[c] == kLostWhole) st = gob[c] < gob[b] ? 1 : 2;
+                    else {
+                        ok = false;  // partly lost: classes vary inside the cell
+                        break;
+                    }
+                }
+                k |= st << (2 * j);
+            }
+            if (ok) key[b] = k;
+        }
+}
 
 // Frame descriptors and the workspace buffers they point into.
 int setup_frames(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
@@ -442,7 +504,7 @@ int setup_frames(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
         rc = ctx->dev_reserve(ws.trace, sizeof(int16_t) * std::max<size_t>(
                                             (size_t)b.nblocks * std::max(p->iters, 1), 1));
     if (!rc) rc = ctx->dev_reserve(ws.work, sizeof(float) * work_floats);
-    if (!rc) rc = ctx->dev_reserve(ws.lost, b.nblocks);
+    if (!rc) rc = ctx->dev_reserve(ws.lost, 2 * (size_t)b.nblocks);  // any lost, part intact
     if (!rc) rc = ctx->dev_reserve(ws.lost_off, sizeof(int) * (n + 1));
     if (!rc) rc = ctx->dev_reserve(ws.gob, sizeof(int32_t) * b.nblocks);
     if (!rc) rc = ctx->dev_reserve(ws.status, sizeof(int) * 4);
@@ -499,7 +561,7 @@ int block_loss_maps(fse_ctx *ctx, Workspace &ws, int n, const fse_params *p, cud
     int max_rows_x_bw = 0;
     for (int i = 0; i < n; ++i) max_rows_x_bw = std::max(max_rows_x_bw, fd[i].H * fd[i].bw);
     rc = ctx->host_reserve(ws.stage, sizeof(FrameDesc) * n + sizeof(int) * (n + 1) +
-                                         b.nblocks + 64);
+                                         2 * (size_t)b.nblocks + 64);
     if (rc) return rc;
     char *st = static_cast<char *>(ws.stage.ptr);
     std::memcpy(st, fd.data(), sizeof(FrameDesc) * n);
@@ -508,21 +570,23 @@ int block_loss_maps(fse_ctx *ctx, Workspace &ws, int n, const fse_params *p, cud
                        stream));
     CK(cudaMemcpyAsync(ws.lost_off.ptr, st + sizeof(FrameDesc) * n, sizeof(int) * (n + 1),
                        cudaMemcpyHostToDevice, stream));
-    CK(cudaMemsetAsync(ws.lost.ptr, 0, b.nblocks, stream));
-    CK(launch_block_loss(static_cast<FrameDesc *>(ws.frames.ptr), n, max_rows_x_bw,
-                         static_cast<uint8_t *>(ws.lost.ptr),
-                         static_cast<int *>(ws.lost_off.ptr), stream));
+    CK(cudaMemsetAsync(ws.lost.ptr, 0, 2 * (size_t)b.nblocks, stream));
+    uint8_t *d_lost = static_cast<uint8_t *>(ws.lost.ptr);
+    CK(launch_block_loss(static_cast<FrameDesc *>(ws.frames.ptr), n, max_rows_x_bw, d_lost,
+                         d_lost + b.nblocks, static_cast<int *>(ws.lost_off.ptr), stream));
     b.map_kernel = true;
     uint8_t *lost_stage =
         reinterpret_cast<uint8_t *>(st + sizeof(FrameDesc) * n + sizeof(int) * (n + 1));
     int *err_stage = reinterpret_cast<int *>(
-        (reinterpret_cast<uintptr_t>(lost_stage + b.nblocks) + 15) & ~(uintptr_t)15);
-    CK(cudaMemcpyAsync(lost_stage, ws.lost.ptr, b.nblocks, cudaMemcpyDeviceToHost, stream));
+        (reinterpret_cast<uintptr_t>(lost_stage + 2 * (size_t)b.nblocks) + 15) & ~(uintptr_t)15);
+    CK(cudaMemcpyAsync(lost_stage, d_lost, 2 * (size_t)b.nblocks, cudaMemcpyDeviceToHost,
+                       stream));
     if (ws.status_live)
         CK(cudaMemcpyAsync(err_stage, static_cast<int *>(ws.status.ptr) + 1, sizeof(int),
                            cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
-    std::memcpy(b.lost.data(), lost_stage, b.nblocks);
+    for (int k = 0; k < b.nblocks; ++k)
+        b.lost[k] = lost_stage[k] ? (lost_stage[b.nblocks + k] ? kLostPart : kLostWhole) : 0;
     if (ws.status_live && *err_stage) {
         ws.status_live = false;
         return FSE_ETIMEDOUT;
@@ -539,6 +603,8 @@ int plan_frames(fse_ctx *ctx, int n, const fse_params *p, Batch &b) {
     b.depths.assign(n, FrameDepths{});
     std::vector<int> plan_rc(n, FSE_OK);
     const int rad = kBorder >> block_log2(p->block);
+    const bool keys = wtables_apply(ctx, p);
+    b.wkey.assign(keys ? b.nblocks : 0, -1);
     ctx->pool.run(n, [&](int i) {
         const FrameDesc &d = b.fd[i];
         const int nb = d.bh * d.bw;
@@ -556,6 +622,9 @@ int plan_frames(fse_ctx *ctx, int n, const fse_params *p, Batch &b) {
         f.ids = b.ids[i].data();
         f.n = (int)b.ids[i].size();
         frame_depths(f, rad);
+        if (keys)
+            frame_wkeys(d, b.lost.data() + b.lost_off[i], b.gob.data() + b.lost_off[i],
+                        b.wkey.data() + b.lost_off[i]);
     });
     b.max_groups = b.lost_blocks = 0;
     for (int i = 0; i < n; ++i) {
@@ -592,6 +661,80 @@ void claim_order(fse_ctx *ctx, int n, bool persistent, int grid, Batch &b) {
     }
 }
 
+// W tables of the batch's blocks: keys not yet in the context's set for
+// (rho, delta) get a table slot and are filled on `stream` (before the
+// extrapolation); a key that finds no room within the memory budget stays
+// without a table (its block computes W).  b.wptr gets each block's table.
+int wtables_for_batch(fse_ctx *ctx, Workspace &ws, const fse_params *p, const float *rho_tab,
+                      cudaStream_t stream, Batch &b) {
+    b.wptr.assign(b.wkey.empty() ? 0 : b.nblocks, 0);
+    b.tables = false;
+    if (b.wkey.empty()) return FSE_OK;
+    std::lock_guard<std::mutex> lk(ctx->wt_mu);
+    fse_ctx::WTableSet *set = nullptr;
+    for (auto &t : ctx->wsets)
+        if (t.rho == p->rho && t.delta == p->delta) set = &t;
+    if (!set) {
+        ctx->wsets.emplace_back();
+        set = &ctx->wsets.back();
+        set->rho = p->rho;
+        set->delta = p->delta;
+        set->slot.assign(kWKeys, -1);
+    }
+    constexpr int kChunk = 32;  // tables per chunk
+    std::vector<int32_t> new_keys;
+    std::vector<uint64_t> new_dst;
+    for (int k = 0; k < b.nblocks; ++k) {
+        const int key = b.wkey[k];
+        if (key < 0) continue;
+        int s = set->slot[key];
+        if (s < 0) {
+            if (ctx->wchunks.empty() || ctx->wchunk_used == kChunk) {
+                fse::DevBuf c;
+                if (ctx->dev_reserve(c, (size_t)kChunk * kW4Bytes) != FSE_OK) {
+                    b.wkey[k] = -1;  // over budget: this block computes W
+                    continue;
+                }
+                ctx->wchunks.push_back(c);
+                ctx->wchunk_used = 0;
+            }
+            s = (int)set->addr.size();
+            set->addr.push_back(reinterpret_cast<uint64_t>(ctx->wchunks.back().ptr) +
+                                (uint64_t)ctx->wchunk_used * kW4Bytes);
+            ctx->wchunk_used += 1;
+            set->slot[key] = s;
+            new_keys.push_back(key);
+            new_dst.push_back(set->addr[s]);
+        }
+        b.wptr[k] = set->addr[s];
+        b.tables = true;
+    }
+    if (!b.tables) return FSE_OK;
+    // tables filled by batches on other streams are complete before use
+    if (ctx->wt_fill) CK(cudaStreamWaitEvent(stream, ctx->wt_fill, 0));
+    if (!new_keys.empty()) {
+        const size_t nk = new_keys.size();
+        const size_t kbytes = (sizeof(int32_t) * nk + 15) & ~(size_t)15;
+        int rc = ctx->host_reserve(ws.wstage, kbytes + sizeof(uint64_t) * nk);
+        if (!rc) rc = ctx->dev_reserve(ws.wfill, kbytes + sizeof(uint64_t) * nk);
+        if (rc) return rc;
+        char *hs = static_cast<char *>(ws.wstage.ptr);
+        std::memcpy(hs, new_keys.data(), sizeof(int32_t) * nk);
+        std::memcpy(hs + kbytes, new_dst.data(), sizeof(uint64_t) * nk);
+        CK(cudaMemcpyAsync(ws.wfill.ptr, hs, kbytes + sizeof(uint64_t) * nk,
+                           cudaMemcpyHostToDevice, stream));
+        const char *df = static_cast<const char *>(ws.wfill.ptr);
+        CK(launch_wtables(reinterpret_cast<const int32_t *>(df),
+                          reinterpret_cast<const uint64_t *>(df + kbytes), (int)nk, p->delta,
+                          rho_tab, static_cast<const float2 *>(ctx->tw_dev.ptr), stream));
+        if (!ctx->wt_fill) CK(cudaEventCreateWithFlags(&ctx->wt_fill, cudaEventDisableTiming));
+        CK(cudaEventRecord(ctx->wt_fill, stream));
+        // the staging is reused by the next fill of this workspace
+        CK(cudaStreamSynchronize(stream));
+    }
+    return FSE_OK;
+}
+
 // Descriptors, group maps, items and TMA descriptors to the device through
 // the pinned staging buffer; completion flags cleared.
 int upload_batch(fse_ctx *ctx, Workspace &ws, int n, bool persistent, cudaStream_t stream,
@@ -599,7 +742,11 @@ int upload_batch(fse_ctx *ctx, Workspace &ws, int n, bool persistent, cudaStream
     const size_t n_items = b.items.size();
     int rc = ctx->dev_reserve(ws.items, sizeof(int2) * std::max<size_t>(n_items, 1));
     if (!rc && persistent) rc = ctx->dev_reserve(ws.done, sizeof(uint32_t) * b.nblocks);
+    if (!rc && b.tables) rc = ctx->dev_reserve(ws.wptr, sizeof(uint64_t) * b.nblocks);
     if (rc) return rc;
+    for (int i = 0; i < n; ++i)
+        b.fd[i].wtab = b.tables ? static_cast<const uint64_t *>(ws.wptr.ptr) + b.lost_off[i]
+                                : nullptr;
     uint32_t *dp = static_cast<uint32_t *>(ws.done.ptr);
     for (int i = 0; i < n; ++i) b.fd[i].done = persistent ? dp + b.lost_off[i] : nullptr;
     // TMA descriptors (frames whose buffers allow it)
@@ -612,7 +759,8 @@ int upload_batch(fse_ctx *ctx, Workspace &ws, int n, bool persistent, cudaStream
                 b.fd[i].tmaps = mp + sizeof(CUtensorMap) * kMapsPerFrame * i;
     }
     const size_t stage_bytes = sizeof(FrameDesc) * n + sizeof(int32_t) * b.nblocks +
-                               sizeof(int2) * n_items + sizeof(CUtensorMap) * maps.size() + 256;
+                               sizeof(int2) * n_items + sizeof(CUtensorMap) * maps.size() +
+                               (b.tables ? sizeof(uint64_t) * b.nblocks : 0) + 256;
     if ((rc = ctx->host_reserve(ws.stage, stage_bytes))) return rc;
     char *st = static_cast<char *>(ws.stage.ptr);
     size_t off = 0;
@@ -630,6 +778,7 @@ int upload_batch(fse_ctx *ctx, Workspace &ws, int n, bool persistent, cudaStream
     if (!rc) rc = put(ws.gob.ptr, b.gob.data(), sizeof(int32_t) * b.nblocks);
     if (!rc) rc = put(ws.items.ptr, b.items.data(), sizeof(int2) * n_items);
     if (!rc && n_items > 0) rc = put(ws.tmaps.ptr, maps.data(), sizeof(CUtensorMap) * maps.size());
+    if (!rc && b.tables) rc = put(ws.wptr.ptr, b.wptr.data(), sizeof(uint64_t) * b.nblocks);
     if (rc) return rc;
     if (persistent && b.nblocks > 0)
         CK(cudaMemsetAsync(ws.done.ptr, 0, sizeof(uint32_t) * b.nblocks, stream));
@@ -677,6 +826,7 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
         stuck_item = (int)n_items - 1;  // waits on a flag nothing sets
         ctx->test_stuck_dep = false;
     }
+    if ((rc = wtables_for_batch(ctx, ws, p, rho_tab, stream, b))) return rc;
     if ((rc = upload_batch(ctx, ws, n, persistent, stream, b))) return rc;
 
     // ---- outputs start as copies of the inputs ----
@@ -794,6 +944,9 @@ void fse::release_workspace(fse_ctx *ctx, Workspace &ws) {
     ctx->dev_release(ws.status);
     ctx->dev_release(ws.tmaps);
     ctx->dev_release(ws.trace);
+    ctx->dev_release(ws.wptr);
+    ctx->dev_release(ws.wfill);
+    ctx->host_release(ws.wstage);
     ctx->dev_release(ws.d_luma);
     ctx->dev_release(ws.d_mask);
     ctx->dev_release(ws.d_out);
@@ -871,6 +1024,8 @@ extern "C" void fse_ctx_destroy(fse_ctx *ctx) {
     ctx->dev_release(ctx->tw_dev);
     for (auto &e : ctx->rho_tabs) ctx->dev_release(e.second);
     for (auto &f : ctx->frags) ctx->dev_release(f);
+    for (auto &c : ctx->wchunks) ctx->dev_release(c);
+    if (ctx->wt_fill) cudaEventDestroy(ctx->wt_fill);
     delete ctx;
 }
 
@@ -1079,6 +1234,12 @@ extern "C" int fse_ctx_set_option(fse_ctx *ctx, int option, long long value) {
         std::lock_guard<std::mutex> lk(ctx->mu);
         if (value < 1 || value > 4096) return FSE_EINVAL;
         ctx->max_batch = (int)value;
+        return FSE_OK;
+    }
+    case FSE_OPT_W_TABLES: {
+        if (value != 0 && value != 1) return FSE_EINVAL;
+        std::lock_guard<std::mutex> lk(ctx->wt_mu);
+        ctx->w_tables = (int)value;
         return FSE_OK;
     }
     case FSE_OPT_SERVE_LATENCY_MS: {

@@ -41,6 +41,9 @@ struct HostBuf {
 // Everything one in-flight batch needs on the device.
 struct Workspace {
     DevBuf frames, work, lost, lost_off, gob, items, done, status, trace;
+    DevBuf wptr;                   // per block: address of its W table, or 0
+    DevBuf wfill;                  // keys and destinations of new W tables
+    HostBuf wstage;                // pinned staging of wfill
     DevBuf tmaps;                  // TMA descriptors of the frames (2 per frame)
     DevBuf d_luma, d_mask, d_out;  // device copies of host frames
     HostBuf stage;                 // pinned staging for uploads / readback
@@ -152,6 +155,23 @@ struct fse_ctx {
     std::map<std::vector<long long>, std::pair<int, int>> tuned;
     int last_executor = 0, last_ctas = 0;  // configuration of the last batch
 
+    // Weight-spectrum tables per (rho, delta): slot[key] indexes addr, the
+    // device address of the key's table (-1: none yet).  Tables live in
+    // chunks that are never moved or freed before the context is destroyed,
+    // so batches in flight on other streams keep valid addresses.  wt_fill
+    // is recorded after every fill; a batch that uses tables waits for it.
+    struct WTableSet {
+        float rho = 0.f, delta = 0.f;
+        std::vector<int32_t> slot;
+        std::vector<uint64_t> addr;
+    };
+    std::vector<WTableSet> wsets;
+    std::vector<fse::DevBuf> wchunks;
+    int wchunk_used = 0;            // tables in the last chunk
+    cudaEvent_t wt_fill = nullptr;
+    std::mutex wt_mu;
+    int w_tables = 1;               // FSE_OPT_W_TABLES
+
     fse::DevBuf tw_dev;                                   // 64 twiddles
     std::vector<std::pair<float, fse::DevBuf>> rho_tabs;  // Eq. (2) decay per (rho, block)
     fse::DevBuf frags[6];                                 // per precision (tensor cores)
@@ -199,7 +219,10 @@ struct fse_ctx {
 };
 
 namespace fse {
-// Block-loss map [bh][bw] of a frame in host memory.
+// Block-loss states: 0 = no lost sample, kLostPart = some in-image samples
+// lost, kLostWhole = every in-image sample lost.
+constexpr uint8_t kLostPart = 1, kLostWhole = 2;
+// Block-loss map [bh][bw] of a frame in host memory (states above).
 std::vector<uint8_t> host_block_loss(const fse_frame &f, int B);
 // ctas_per_sm: persistent CTAs per SM for this batch (< 0: the context's
 // FSE_OPT_PERSISTENT_CTAS setting).

@@ -134,7 +134,26 @@ struct FrameDesc {
     int pad0;
     const void *tmaps;       // 2 tensor maps (luma, mask), 64-byte aligned,
                              // or null: gather with plain loads
+    const uint64_t *wtab;    // [bh*bw] device address of the block's weight-
+                             // spectrum table (W4 layout, kW4Bytes), 0: the
+                             // block computes W itself; null: no tables
 };
+
+// Weight-spectrum tables.  W = DFT64(w) depends only on the sub-area classes
+// of the area (Sec. 2: A, R, B_i, B_o, outside) and on rho and delta.  With
+// B = 16 and a block that is lost as a whole, those classes follow from the
+// states of its eight neighbour blocks: 0 = A (not lost), 1 = R (lost as a
+// whole, earlier group), 2 = B_o (lost as a whole, same or later group),
+// 3 = outside the image.  The key packs them, 2 bits each, neighbours in
+// raster order (dy, dx) = (-1,-1), (-1,0), (-1,1), (0,-1), (0,1), (1,-1),
+// (1,0), (1,1).  A table holds W in the W4 layout of the shared-memory
+// region, kW4Bytes bytes, so that a block copies it in with one bulk copy.
+constexpr int kWKeyStates = 4;
+constexpr int kWKeys = 1 << 16;
+// Fills the tables of `n` keys (FP32 split DFTs, the arithmetic of the
+// in-kernel projection): keys [n] (device), dst [n] table addresses (device).
+cudaError_t launch_wtables(const int32_t *keys, const uint64_t *dst, int n, float delta,
+                           const float *rho_tab, const float2 *tw_tab, cudaStream_t stream);
 
 // Work of the persistent executor: items are (frame, block) pairs in a claim
 // order in which every block follows its dependencies (the earlier-group lost
@@ -151,8 +170,11 @@ struct WorkQueue {
 };
 
 // Launchers (fse_kernels.cu).  All are asynchronous on `stream`.
+// lost_out[b] = 1 when any in-image sample of block b is lost; part_out
+// (optional) [b] = 1 when some in-image sample of b is not lost.  Both start
+// zeroed by the caller.
 cudaError_t launch_block_loss(const FrameDesc *frames_dev, int n_frames,
-                              int max_blocks, uint8_t *lost_out,
+                              int max_blocks, uint8_t *lost_out, uint8_t *part_out,
                               const int *lost_off_dev, cudaStream_t stream);
 cudaError_t launch_group(const FrameDesc *frames_dev, const int2 *items,
                          int n_items, const KParams &kp, const float *rho_tab,

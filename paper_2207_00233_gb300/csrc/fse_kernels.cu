@@ -25,62 +25,12 @@
 
 #include "../../include/fse.h"
 #include "fse_internal.h"
+#include "fse_iter.cuh"
 
 namespace fse {
 namespace {
 
-typedef unsigned long long u64;
-
-// ---- packed FP32 pairs ------------------------------------------------------
-__device__ __forceinline__ u64 pack2(float lo, float hi) {
-    u64 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ float2 unpack2(u64 v) {
-    float2 r;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
-    return r;
-}
-__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
-    u64 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
-    u64 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ u64 add2(u64 a, u64 b) {
-    u64 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
-    u64 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-// |R|^2 of a pair; the same instruction sequence is used wherever an
-// energy is compared, so equal inputs give bit-identical energies.
-__device__ __forceinline__ u64 energy2(u64 re, u64 im) {
-    return fma2(im, im, mul2(re, re));
-}
-__device__ __forceinline__ float max3(float a, float b, float c) {
-    float r;
-    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
-__device__ __forceinline__ void lds_pair(uint32_t addr, u64 &a, u64 &b) {
-    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
-}
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void st_shared_pair(uint32_t addr, u64 a, u64 b) {
-    asm volatile("st.shared.v2.b64 [%0], {%1, %2};" ::"r"(addr), "l"(a), "l"(b) : "memory");
-}
+using namespace fse::iter;  // packed FP32 pairs, W4 addressing, the loop body
 
 // ---- TMA: bulk tensor copies completed on a shared-memory mbarrier ----------
 
@@ -129,8 +79,39 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *map, int x
         "l"(map), "r"(x), "r"(y), "r"(bar)
         : "memory");
 }
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+// from global memory into shared memory at `dst`, completing on `bar`.
+__device__ __forceinline__ void bulk_load(uint32_t dst, uint64_t src, uint32_t bytes,
+                                          uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
 // A TMA copy that has not completed after this long is reported as an error.
 constexpr unsigned long long kStageLimitNs = 2000000000ull;
+
+// Copies a weight-spectrum table (kW4Bytes, W4 layout) into the W4 region
+// with one bulk copy on the CTA's staging mbarrier (initialised, its next
+// phase parity at kMbarOff + 8).  All threads call it after a barrier that
+// ends every use of the region.  Returns false on every thread when the copy
+// did not complete within kStageLimitNs; the copy in flight is then waited
+// for once more, so that it does not land after the caller moves on.
+__device__ __forceinline__ bool load_wtable(unsigned char *smem, uint64_t table) {
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(smem + kMbarOff);
+    volatile uint32_t *phase = reinterpret_cast<volatile uint32_t *>(smem + kMbarOff + 8);
+    const uint32_t ph = *phase;
+    if (threadIdx.x == 0) {
+        // the region's earlier generic accesses come before the async copy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(bar, kW4Bytes);
+        bulk_load((uint32_t)__cvta_generic_to_shared(smem), table, kW4Bytes, bar);
+    }
+    const bool ok = __syncthreads_and(mbar_wait(bar, ph, kStageLimitNs));
+    if (!ok) mbar_wait(bar, ph, kStageLimitNs);
+    if (threadIdx.x == 0) *phase = ph ^ 1u;
+    return ok;
+}
 
 // ---- sources: where an area comes from and where its result goes -----------
 
@@ -218,6 +199,12 @@ struct FrameSrc {
         }
     }
 
+    // Device address of the block's weight-spectrum table, 0 if it has none.
+    __device__ __forceinline__ uint64_t table() const {
+        const uint64_t *t = fd.wtab;
+        return t ? t[self] : 0ull;
+    }
+
     // Thread t holds the model value of sample (t / 16, t % 16) of the block.
     __device__ void store(float g) const {
         const int i = threadIdx.x >> 4, j = threadIdx.x & 15;
@@ -253,6 +240,7 @@ struct AreaSrc {
         }
     }
     __device__ void store(float gv) const { g[threadIdx.x] = gv; }
+    __device__ __forceinline__ uint64_t table() const { return 0ull; }
 };
 
 struct Trace {
@@ -393,9 +381,14 @@ __device__ __forceinline__ void col_dft_step2(const float *ts, const float2 *tw,
     for (int r = 0; r < 8; ++r) ai[r][1] = -ai[r][1];
 }
 
+// kW: also the spectrum of w (wre, wim and the real columns of W at
+// kXrwOff); without it only R_w, for a block whose W comes from a table
+// (the rows of w f take the same arithmetic either way).
+template <bool kW>
 __device__ __forceinline__ void project_fp32(unsigned char *smem, const float2 *tw,
                                              u64 (&rre)[8], u64 (&rim)[8],
                                              float (&wre)[8][2], float (&wim)[8][2]) {
+    constexpr int kRows = kW ? kYRows : kArea;  // rows of the row DFTs
     const float *xt = reinterpret_cast<const float *>(smem + kXTileOff);
     const float *wt = reinterpret_cast<const float *>(smem + kWTileOff);
     float2 *yx = reinterpret_cast<float2 *>(smem + kYxOff);
@@ -410,8 +403,8 @@ __device__ __forceinline__ void project_fp32(unsigned char *smem, const float2 *
     // Step A: item (b, row) (lanes: consecutive rows) stores Z[b][0], Z[b][4]
     // and Z[b][1..3] as eight planes zs[8b + slot][row].
     float *zs = reinterpret_cast<float *>(smem + kZsOff);
-    for (int it = tid; it < 8 * kYRows; it += kThreads) {
-        const int bb = it / kYRows, row = it - bb * kYRows;
+    for (int it = tid; it < 8 * kRows; it += kThreads) {
+        const int bb = it / kRows, row = it - bb * kRows;
         const float *src = (row < kArea ? xt + row * kTileStride : wt + (row - kArea) * kTileStride);
         float v[6];
 #pragma unroll
@@ -435,8 +428,8 @@ __device__ __forceinline__ void project_fp32(unsigned char *smem, const float2 *
     __syncthreads();
     // Step B: item (r, row) (lanes: consecutive rows, r warp-uniform) sums
     // Y[r + 8q] for every q with r + 8q <= 32.
-    for (int it = tid; it < 8 * kYRows; it += kThreads) {
-        const int r = it / kYRows, row = it - r * kYRows;
+    for (int it = tid; it < 8 * kRows; it += kThreads) {
+        const int r = it / kRows, row = it - r * kRows;
         const int rr = r <= 4 ? r : 8 - r;  // conj(Z[b][8 - r]) for r > 4
         const float sgn = r <= 4 ? 1.f : -1.f;
         float yr[5], yi[5];
@@ -479,10 +472,10 @@ __device__ __forceinline__ void project_fp32(unsigned char *smem, const float2 *
     float *tsw = reinterpret_cast<float *>(smem + kTswOff);
     float2 *xrx = reinterpret_cast<float2 *>(smem + kXrOff);
     col_dft_step1(yx, tsx, tw, w, l);
-    col_dft_step1(yw, tsw, tw, w, l);
+    if (kW) col_dft_step1(yw, tsw, tw, w, l);
     if (tid < 2 * kHalfCols) {
         col_dft_real(yx, xrx, tw, tid);
-        col_dft_real(yw, reinterpret_cast<float2 *>(smem + kXrwOff), tw, tid);
+        if (kW) col_dft_real(yw, reinterpret_cast<float2 *>(smem + kXrwOff), tw, tid);
     }
     __syncthreads();
     {
@@ -506,7 +499,7 @@ __device__ __forceinline__ void project_fp32(unsigned char *smem, const float2 *
     // W's real columns are taken from xr when W is stored (store_w4): after
     // a selection of a self-conjugate index (the DC term, say) the residual
     // stays conjugate-symmetric only if W is.
-    col_dft_step2(tsw, tw, w, l, wre, wim);
+    if (kW) col_dft_step2(tsw, tw, w, l, wre, wim);
 }
 
 // ---- projection on the tensor cores (warp-level mma.sync) --------------------
@@ -854,34 +847,6 @@ __device__ __forceinline__ void store_w4(unsigned char *smem, const float (&wre)
     }
 }
 
-// One pass over the thread's entries: R -= dc * W[k - u] (dc = 0 leaves R
-// bit-identical) and the thread's largest |R|^2.
-__device__ __forceinline__ float update_and_max(uint32_t wbase, u64 ndcr2, u64 dci2,
-                                                u64 ndci2, u64 (&rre)[8], u64 (&rim)[8]) {
-    float mx = 0.f;
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        u64 wr, wi;
-        lds_pair(wbase + r * (kDft * 16), wr, wi);
-        u64 a = fma2(wr, ndcr2, rre[r]);
-        a = fma2(wi, dci2, a);
-        u64 b = fma2(wi, ndcr2, rim[r]);
-        b = fma2(wr, ndci2, b);
-        rre[r] = a;
-        rim[r] = b;
-        const float2 e = unpack2(energy2(a, b));
-        mx = max3(mx, e.x, e.y);
-    }
-    return mx;
-}
-
-__device__ __forceinline__ uint32_t w4_base(uint32_t w4addr, int um, int un) {
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const int row = (8 * w - um) & (kDft - 1);
-    const int col = (l - un) & (kDft - 1);
-    return w4addr + (uint32_t)(row * kDft + col) * 16u;
-}
-
 // The full per-block computation.  Returns the model value of this thread's
 // sample of the centre block (unclamped).
 template <int P, bool kTrace, class Src>
@@ -904,11 +869,23 @@ __device__ __forceinline__ float run_block(const Src &src, const KParams &kp,
     u64 rre[8], rim[8];
     if (P == FSE_PREC_FP32) {
         float wre[8][2], wim[8][2];
-        project_fp32(smem, tw, rre, rim, wre, wim);
-        __syncthreads();  // all reads of the stage-1 scratch are done
-        const float2 *xrw = reinterpret_cast<const float2 *>(smem + kXrwOff);
-        store_w4(smem, wre, wim, xrw);
-        if (tid == 0) misc[0] = xrw[0].x;  // W[0] = sum of the weights
+        // W from the block's table (bulk copy; needs the staging mbarrier,
+        // which exists when shared memory starts 128-byte aligned) or
+        // computed here
+        const uint64_t wtab = ((smem_addr(smem) & 127u) == 0u) ? src.table() : 0ull;
+        if (wtab) {
+            project_fp32<false>(smem, tw, rre, rim, wre, wim);
+            __syncthreads();  // all reads of the projection scratch are done
+            if (!load_wtable(smem, wtab) && tid == 0 && kp.error)
+                atomicExch(kp.error, FSE_ETIMEDOUT);
+            if (tid == 0) misc[0] = reinterpret_cast<const float4 *>(smem)[0].x;  // W[0]
+        } else {
+            project_fp32<true>(smem, tw, rre, rim, wre, wim);
+            __syncthreads();  // all reads of the stage-1 scratch are done
+            const float2 *xrw = reinterpret_cast<const float2 *>(smem + kXrwOff);
+            store_w4(smem, wre, wim, xrw);
+            if (tid == 0) misc[0] = xrw[0].x;  // W[0] = sum of the weights
+        }
     } else {
         float wacc[5][4];
         project_mma<P>(smem, kp.frags, rre, rim, wacc);
@@ -926,48 +903,10 @@ __device__ __forceinline__ float run_block(const Src &src, const KParams &kp,
     uint32_t wbase = w4_base(w4addr, 0, 0);
     for (int it = 0; it < K; ++it) {
         const float tmx = update_and_max(wbase, ndcr2, dci2, ndci2, rre, rim);
-        const uint32_t wmx = __reduce_max_sync(0xffffffffu, __float_as_uint(tmx));
-        if (l == 0) smax[w] = wmx;
-        __syncthreads();
-        // lanes 0..7 read the eight warp maxima in one access
-        const uint32_t estar =
-            __reduce_max_sync(0xffffffffu, l < kWarps ? smax[l] : 0u);
-
-        // Smallest linear index whose energy equals the maximum.  Only the
-        // warps that hold the maximum search (a warp-uniform branch).
-        if (__any_sync(0xffffffffu, __float_as_uint(tmx) == estar)) {
-            uint32_t kk = 0xffffffffu;
-            float cre = 0.f, cim = 0.f;
-            if (__float_as_uint(tmx) == estar) {
-#pragma unroll
-                for (int r = 7; r >= 0; --r) {
-                    const float2 e = unpack2(energy2(rre[r], rim[r]));
-                    const float2 re = unpack2(rre[r]), im = unpack2(rim[r]);
-                    if (__float_as_uint(e.y) == estar) {
-                        kk = (uint32_t)((8 * w + r) * kDft + l + 32);
-                        cre = re.y;
-                        cim = im.y;
-                    }
-                    if (__float_as_uint(e.x) == estar) {
-                        kk = (uint32_t)((8 * w + r) * kDft + l);
-                        cre = re.x;
-                        cim = im.x;
-                    }
-                }
-            }
-            // the lane holding the warp's smallest index writes its candidate
-            const uint32_t wk = __reduce_min_sync(0xffffffffu, kk);
-            if (kk == wk) cand[w] = make_float4(__uint_as_float(wk), cre, cim, 0.f);
-        } else if (l == 0) {
-            cand[w].x = __uint_as_float(0xffffffffu);
-        }
-        __syncthreads();
-        // lanes 0..7 read the eight warp candidates; the smallest index wins.
-        // Warp w owns indices [512 w, 512 w + 512), so the winner's slot is u >> 9.
-        const uint32_t u = __reduce_min_sync(
-            0xffffffffu, l < kWarps ? __float_as_uint(cand[l].x) : 0xffffffffu);
-        const float4 cw = cand[(u >> 9) & (kWarps - 1)];
-        const float dcr = cw.y * gw, dci = cw.z * gw;
+        uint32_t u;
+        float ure, uim;
+        select_two_barriers(tmx, rre, rim, smax, cand, u, ure, uim);
+        const float dcr = ure * gw, dci = uim * gw;
         if (tid == 0) {
             dcl[it] = make_float2(dcr, dci);
             ul[it] = (uint16_t)u;
@@ -1120,9 +1059,9 @@ k_group(const FrameDesc *frames, const int2 *items, KParams kp, const float *rho
         const int2 item = items[blockIdx.x];
         const FrameDesc &fd = frames[item.x];
         const unsigned char *stage = nullptr;
+        if (stage_capable(smem)) stage_init(smem);  // staging and table copies
+        __syncthreads();
         if (fd.tmaps && kp.error && stage_capable(smem)) {
-            stage_init(smem);
-            __syncthreads();
             if (!stage_area(fd, item.y, smem)) {
                 if (threadIdx.x == 0) atomicExch(kp.error, FSE_ETIMEDOUT);
                 return;
@@ -1253,9 +1192,48 @@ k_areas(const float *area_f, const uint8_t *area_cls, KParams kp, const float *r
     src.store(g);
 }
 
+// Weight-spectrum tables: one CTA per key builds the 48x48 weights of the
+// class pattern the key encodes (Eq. (2): rho^dist on A, delta rho^dist on
+// R, 0 on B_i, B_o and outside), takes its DFT with the same FP32 split DFTs
+// as the per-block kernels (so a table equals the W a block would compute)
+// and writes the W4 region to the table.
+__global__ void __launch_bounds__(kThreads, 3)
+k_wtable(const int32_t *keys, const uint64_t *dst, float delta, const float *rho_tab,
+         const float2 *tw_tab) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    float2 *tw = reinterpret_cast<float2 *>(smem + kTwOff);
+    if (threadIdx.x < kDft) tw[threadIdx.x] = tw_tab[threadIdx.x];
+    const int key = keys[blockIdx.x];
+    float *xt = reinterpret_cast<float *>(smem + kXTileOff);
+    float *wt = reinterpret_cast<float *>(smem + kWTileOff);
+    for (int p = threadIdx.x; p < kArea * kArea; p += kThreads) {
+        const int m = p / kArea, n = p - m * kArea;
+        const int cell = (m >> 4) * 3 + (n >> 4);  // 3x3 cells of 16x16, centre 4
+        float w = 0.f;
+        if (cell != 4) {
+            const int st = (key >> (2 * (cell < 4 ? cell : cell - 1))) & 3;
+            if (st == 0) w = rho_tab[p];
+            else if (st == 1) w = delta * rho_tab[p];
+        }
+        xt[m * kTileStride + n] = 0.f;
+        wt[m * kTileStride + n] = w;
+    }
+    __syncthreads();
+    u64 rre[8], rim[8];
+    float wre[8][2], wim[8][2];
+    project_fp32<true>(smem, tw, rre, rim, wre, wim);
+    __syncthreads();
+    store_w4(smem, wre, wim, reinterpret_cast<const float2 *>(smem + kXrwOff));
+    __syncthreads();
+    uint4 *out = reinterpret_cast<uint4 *>(dst[blockIdx.x]);
+    const uint4 *src = reinterpret_cast<const uint4 *>(smem);
+    for (int i = threadIdx.x; i < kW4Bytes / 16; i += kThreads) out[i] = src[i];
+}
+
 // Block-loss map: one thread per (frame, sample row, block column) scans the
 // 16 samples of that block row.
-__global__ void k_block_loss(const FrameDesc *frames, uint8_t *lost, const int *lost_off) {
+__global__ void k_block_loss(const FrameDesc *frames, uint8_t *lost, uint8_t *part,
+                             const int *lost_off) {
     const FrameDesc &fd = frames[blockIdx.y];
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= fd.H * fd.bw) return;
@@ -1263,9 +1241,14 @@ __global__ void k_block_loss(const FrameDesc *frames, uint8_t *lost, const int *
     const int B = 1 << fd.lb;
     const uint8_t *row = fd.mask + (size_t)y * fd.stride + bx * B;
     const int n = min(B, fd.W - bx * B);
-    int any = 0;
-    for (int i = 0; i < n; ++i) any |= row[i];
-    if (any) lost[lost_off[blockIdx.y] + (y >> fd.lb) * fd.bw + bx] = 1;
+    int any = 0, all = 1;
+    for (int i = 0; i < n; ++i) {
+        any |= row[i];
+        all &= row[i] != 0;
+    }
+    const int b = lost_off[blockIdx.y] + (y >> fd.lb) * fd.bw + bx;
+    if (any) lost[b] = 1;
+    if (part && !all) part[b] = 1;
 }
 
 }  // namespace
@@ -1312,8 +1295,11 @@ static cudaError_t ensure_attrs(int precision) {
         r = cudaFuncSetAttribute(k_persistent<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  max_smem);
         if (r != cudaSuccess) return r;
-        return cudaFuncSetAttribute(k_areas<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    max_smem);
+        r = cudaFuncSetAttribute(k_areas<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 max_smem);
+        if (r != cudaSuccess) return r;
+        return cudaFuncSetAttribute(k_wtable, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    smem_bytes(0));
     });
     if (e == cudaSuccess && bit) g_attr_done[precision].fetch_or(bit, std::memory_order_release);
     return e;
@@ -1352,11 +1338,20 @@ int max_resident_ctas(int iters) {
 }
 
 cudaError_t launch_block_loss(const FrameDesc *frames_dev, int n_frames, int max_rows_x_bw,
-                              uint8_t *lost_out, const int *lost_off_dev,
+                              uint8_t *lost_out, uint8_t *part_out, const int *lost_off_dev,
                               cudaStream_t stream) {
     if (n_frames <= 0 || max_rows_x_bw <= 0) return cudaSuccess;
     dim3 grid((max_rows_x_bw + 255) / 256, n_frames);
-    k_block_loss<<<grid, 256, 0, stream>>>(frames_dev, lost_out, lost_off_dev);
+    k_block_loss<<<grid, 256, 0, stream>>>(frames_dev, lost_out, part_out, lost_off_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wtables(const int32_t *keys, const uint64_t *dst, int n, float delta,
+                           const float *rho_tab, const float2 *tw_tab, cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    cudaError_t e = ensure_attrs(FSE_PREC_FP32);
+    if (e != cudaSuccess) return e;
+    k_wtable<<<n, kThreads, smem_bytes(0), stream>>>(keys, dst, delta, rho_tab, tw_tab);
     return cudaGetLastError();
 }
 

@@ -150,6 +150,7 @@ extern "C" int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_param
     h_desc.lb = block_log2(kBlock);
     h_desc.pad0 = 0;
     h_desc.tmaps = nullptr;  // plain-load gather
+    h_desc.wtab = nullptr;   // every block computes its weight spectrum
     na_twiddles(h_tw);
     const double cm = 0.5 * (kArea - 1);
     for (int m = 0; m < kArea; ++m)
@@ -166,7 +167,7 @@ extern "C" int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_param
     NA_CK(cudaMemcpyAsync(d_lost_off, h_lost_off, sizeof(h_lost_off), cudaMemcpyHostToDevice,
                           stream));
     NA_CK(cudaMemsetAsync(d_lost, 0, (size_t)bw * bh, stream));
-    NA_CK(launch_block_loss(d_desc, 1, H * bw, d_lost, d_lost_off, stream));
+    NA_CK(launch_block_loss(d_desc, 1, H * bw, d_lost, nullptr, d_lost_off, stream));
     NA_CK(cudaMemcpyAsync(h_lost, d_lost, (size_t)bw * bh, cudaMemcpyDeviceToHost, stream));
     NA_CK(cudaStreamSynchronize(stream));
 

@@ -503,3 +503,30 @@ def test_host_async_pipeline(fse, ctx):
     finally:
         ctx.fse_ctx_set_option(fse.FSE_OPT_SPIN_LIMIT, 1 << 23)
         ctx.fse_ctx_set_option(fse.FSE_OPT_TEST_STUCK_DEP, 0)
+
+
+def test_w_tables_change_no_byte(fse, ctx):
+    """FSE_OPT_W_TABLES: blocks whose sub-area classes follow from their
+    eight neighbours take W from a per-pattern table computed once per
+    context (FP32, the blocks' own arithmetic).  Outputs and FP32 working
+    values are byte-identical to every block computing W itself, for the
+    first call (tables filled) and a second one (tables reused), in both
+    executors; frames with partial edge blocks and pixel-granular losses mix
+    blocks with and without tables."""
+    frames = fse_synth.workload_batch_1080p(2) + [fse_synth.random_frame(200, 264, 0.3, 91)]
+    img, _ = fse_synth.workload_mixed_512()[0]
+    rng = np.random.default_rng(92)
+    pix = (rng.random(img.shape) < 0.02).astype(np.uint8)
+    pix[100:164, 200:280] = 1
+    frames.append((img, pix))
+    for ex in ("persistent", "groups"):
+        p = _params(fse, 200, 1, ex)
+        ctx.fse_ctx_set_option(fse.FSE_OPT_W_TABLES, 0)
+        try:
+            ref_out, ref_work = gpu_conceal(ctx, frames, p)
+        finally:
+            ctx.fse_ctx_set_option(fse.FSE_OPT_W_TABLES, 1)
+        for _ in range(2):
+            out, work = gpu_conceal(ctx, frames, p)
+            for a, b in zip(ref_out + ref_work, out + work):
+                assert np.array_equal(a, b, equal_nan=True), ex
