@@ -47,7 +47,7 @@ FP32_LANES = 128
 # DRAM bytes (read + write) of one k_persistent<FP32> launch on this workload,
 # from the committed ncu capture of this kernel on this workload (profiles/);
 # None while the kernel differs from the captured one
-TRAFFIC_BYTES_PER_LAUNCH = 190.454528e6 + 53.233664e6
+TRAFFIC_BYTES_PER_LAUNCH = None
 
 
 def parse():
@@ -647,7 +647,7 @@ def main():
     torch.cuda.synchronize()
     lost_blocks = ctx.fse_last_batch_info()["lost_blocks"]
     launches_per_step = ctx.fse_last_batch_info()["launches"]
-    launch_cfg = ctx.fse_last_batch_config()
+    launch_cfg = ctx.fse_last_batch_shape()
 
     # ---- timed region: device time of each step, L2 flushed in between ----
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -805,7 +805,12 @@ def main():
                        "height": 1080, "width": 1920, "iters": K_ITERS, "order": "optimized",
                        "executor": ("persistent" if launch_cfg["executor"] == fse.FSE_EXEC_PERSISTENT
                                     else "levels"),
-                       "ctas_per_sm": launch_cfg["ctas_per_sm"], "autotuned": not args.no_autotune,
+                       "ctas_per_sm": launch_cfg["ctas_per_sm"],
+                       "claim_order": {0: "delayed height", 1: "height", 2: "list schedule"}[
+                           launch_cfg["claim_order"]],
+                       "threads_per_cta": launch_cfg["threads_per_cta"],
+                       "autotuned": not args.no_autotune,
+                       "w_tables": "tensor-core DFT-as-GEMM, once per class pattern (cached)",
                        "planning": "overlapped with the previous step (inputs ready)",
                        "precision": args.precision,
                        "lost_blocks_per_step": lost_blocks, "lost_pixels_per_step": lost_pixels,

@@ -305,6 +305,14 @@ int fse_recent_kernel_ms(fse_ctx *ctx, int n, float *ms, int *count);
  * FSE_EXEC_GROUPS).  Either pointer may be NULL.  Errors: FSE_EINVAL. */
 int fse_last_batch_config(fse_ctx *ctx, int *executor, int *ctas_per_sm);
 
+/* The full launch shape of the last fse_conceal_batch / _host call: as
+ * fse_last_batch_config, plus *claim_order (FSE_CLAIM_*, the persistent
+ * executor's claim order; 0 for FSE_EXEC_GROUPS), *threads_per_cta (256:
+ * one thread owns 16 spectrum entries) and *blocks_per_cta (1).  Any pointer
+ * may be NULL.  Errors: FSE_EINVAL. */
+int fse_last_batch_shape(fse_ctx *ctx, int *executor, int *ctas_per_sm, int *claim_order,
+                         int *threads_per_cta, int *blocks_per_cta);
+
 /* Device time of the extrapolation launches of the last fse_conceal_batch
  * or fse_conceal_batch_host call (the persistent kernel, or all group
  * launches), from CUDA events recorded on the call's stream around them.
@@ -361,6 +369,25 @@ int fse_copy_trace(fse_ctx *ctx, int frame, int16_t *dst, void *cuda_stream);
 int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_params *params,
                               void *cuda_stream);
 
+/* Weight-spectrum table of one class pattern (inspection; what
+ * FSE_OPT_W_TABLES gives the blocks of that pattern): W = DFT64 of the 48x48
+ * weights of Eq. (2) (Sec. 2 sub-areas: the 16x16 centre is B_i, each of the
+ * eight neighbour cells is A, R, B_o or outside as the key says; see
+ * FSE_OPT_W_TABLES), written to dst (DEVICE pointer, 16-byte aligned,
+ * 72,704 bytes) as 71 rows of 64 float4 (Re W[r][c], Re W[r][c ^ 32],
+ * Im W[r][c], Im W[r][c ^ 32]), rows 64..70 repeating rows 0..6.
+ * key: 16 bits, two per neighbour in raster order (dy, dx) = (-1,-1),
+ * (-1,0), (-1,1), (0,-1), (0,1), (1,-1), (1,0), (1,1); 0 = A (not lost),
+ * 1 = R (concealed earlier), 2 = B_o (lost, later), 3 = outside the image.
+ * builder: 1 = the FP32 split DFTs of the block kernels, 2 = DFT-as-GEMM on
+ * the tcgen05 tensor cores (split-TF32 operands, FP32 accumulation).
+ * Synchronises `cuda_stream`.
+ * Errors: FSE_EINVAL (bad key, rho outside (0, 1), delta outside [0, 1],
+ * builder, NULL or unaligned dst), FSE_ENOMEM, FSE_ECUDA, FSE_ETIMEDOUT (a
+ * tensor-core product did not complete within its bounded wait). */
+int fse_weight_table(fse_ctx *ctx, int key, float rho, float delta, int builder, void *dst,
+                     void *cuda_stream);
+
 /* Context options (host-side settings; take effect on the next batch).
  *   FSE_OPT_SPIN_LIMIT       polls a device-side dependency wait makes
  *                            before it gives up with FSE_ETIMEDOUT
@@ -383,11 +410,13 @@ int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_params *params,
  *                            (frames, samples, K, B, order, precision), the
  *                            fastest of the launch configurations whose
  *                            results are identical: the persistent launch
- *                            with 1 .. (occupancy limit) CTAs per SM, or one
- *                            launch per dependency level.  The first call of
- *                            a shape runs one untimed pass, then times every
+ *                            with 1 .. (occupancy limit) CTAs per SM and
+ *                            each claim order (FSE_CLAIM_*), or one launch
+ *                            per dependency level.  The first call of a
+ *                            shape runs one untimed pass, then times every
  *                            candidate twice (same output bytes); later
- *                            calls reuse the choice.
+ *                            calls reuse the choice (fse_last_batch_shape
+ *                            reports it).
  *                            0 (default): as requested.
  *   FSE_OPT_INPUTS_READY     1: the loss masks of each fse_conceal_batch call
  *                            are complete when the call is made (no work
@@ -406,16 +435,29 @@ int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_params *params,
  *                            the budget instead of growing without bound.
  *                            0 (default): admission by queue length and
  *                            memory only.
- *   FSE_OPT_W_TABLES         1 (default): blocks whose sub-area classes are
- *                            fixed by their eight neighbours (16x16 blocks
- *                            lost as a whole, FP32 projection) take the
- *                            spectrum of their weights, W, from a table per
- *                            class pattern, computed once per context and
+ *   FSE_OPT_CLAIM_ORDER      order in which the persistent executor's CTAs
+ *                            claim blocks (every order gives the same
+ *                            bytes: a block waits only for the
+ *                            earlier-group blocks in its area):
+ *                            FSE_CLAIM_DELAYED (default) the longest chain
+ *                            of dependants first, cut into rounds of one
+ *                            claim per CTA, each block moved past its
+ *                            dependencies' round; FSE_CLAIM_HEIGHT the
+ *                            longest chain first; FSE_CLAIM_LIST a list
+ *                            schedule of rounds of ready blocks.
+ *   FSE_OPT_W_TABLES         blocks whose sub-area classes are fixed by
+ *                            their eight neighbours (16x16 blocks lost as a
+ *                            whole, FP32 projection) take the spectrum of
+ *                            their weights, W, from a table per class
+ *                            pattern, computed once per context and
  *                            (rho, delta) and kept in device memory within
  *                            the memory budget (72,704 bytes per pattern);
  *                            the block kernels then project only w f.
- *                            The tables equal what the blocks compute.
- *                            0: every block computes W.
+ *                            2 (default): tables by DFT-as-GEMM on the
+ *                            tcgen05 tensor cores (split-TF32, FP32
+ *                            accumulation; FP32-grade); 1: tables by the
+ *                            blocks' own FP32 split DFTs (byte-identical to
+ *                            0); 0: every block computes W.
  * Errors: FSE_EINVAL for an unknown option or value. */
 #define FSE_OPT_SPIN_LIMIT 1
 #define FSE_OPT_PERSISTENT_CTAS 2
@@ -428,6 +470,10 @@ int fse_conceal_frame_noalloc(const fse_frame *frame, const fse_params *params,
 #define FSE_OPT_INPUTS_READY 9
 #define FSE_OPT_SERVE_LATENCY_MS 10
 #define FSE_OPT_W_TABLES 11
+#define FSE_OPT_CLAIM_ORDER 12
+#define FSE_CLAIM_DELAYED 0
+#define FSE_CLAIM_HEIGHT 1
+#define FSE_CLAIM_LIST 2
 int fse_ctx_set_option(fse_ctx *ctx, int option, long long value);
 
 const char *fse_strerror(int status);

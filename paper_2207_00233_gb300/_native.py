@@ -25,12 +25,13 @@ EXPORTED = [
     "fse_plan_order", "fse_plan_claims", "fse_ctx_create", "fse_ctx_destroy", "fse_conceal_batch",
     "fse_conceal_batch_host", "fse_conceal_batch_host_async", "fse_wait_batch",
     "fse_extrapolate_areas", "fse_submit", "fse_poll",
-    "fse_drain", "fse_last_batch_info", "fse_last_batch_config", "fse_ctx_set_option", "fse_copy_work", "fse_copy_trace", "fse_last_kernel_ms", "fse_recent_kernel_ms", "fse_conceal_frame_noalloc", "fse_measure_peaks", "fse_loop_microbench", "fse_strerror",
+    "fse_drain", "fse_last_batch_info", "fse_last_batch_config", "fse_last_batch_shape", "fse_ctx_set_option", "fse_copy_work", "fse_copy_trace", "fse_last_kernel_ms", "fse_recent_kernel_ms", "fse_conceal_frame_noalloc", "fse_measure_peaks", "fse_loop_microbench", "fse_weight_table", "fse_strerror",
 ]
 FSE_OPT_SPIN_LIMIT, FSE_OPT_PERSISTENT_CTAS, FSE_OPT_SERVE_SLOTS = 1, 2, 3
 FSE_OPT_SERVE_MAX_BATCH, FSE_OPT_TEST_STUCK_DEP, FSE_OPT_KEEP_TRACE = 4, 5, 6
 FSE_OPT_GROUP_LAUNCHES, FSE_OPT_AUTOTUNE, FSE_OPT_INPUTS_READY = 7, 8, 9
-FSE_OPT_SERVE_LATENCY_MS, FSE_OPT_W_TABLES = 10, 11
+FSE_OPT_SERVE_LATENCY_MS, FSE_OPT_W_TABLES, FSE_OPT_CLAIM_ORDER = 10, 11, 12
+FSE_CLAIM_DELAYED, FSE_CLAIM_HEIGHT, FSE_CLAIM_LIST = 0, 1, 2
 
 
 class fse_params(ctypes.Structure):
@@ -95,10 +96,12 @@ def lib() -> ctypes.CDLL:
     L.fse_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(cint), ctypes.POINTER(fse_stats)]
     L.fse_drain.argtypes = [vp, cint]
     L.fse_last_batch_config.argtypes = [vp, ctypes.POINTER(cint), ctypes.POINTER(cint)]
+    L.fse_last_batch_shape.argtypes = [vp] + [ctypes.POINTER(cint)] * 5
     L.fse_recent_kernel_ms.argtypes = [vp, cint, vp, ctypes.POINTER(cint)]
     L.fse_last_batch_info.argtypes = [vp, ctypes.POINTER(cint), ctypes.POINTER(cint),
                                       ctypes.POINTER(cint)]
     L.fse_ctx_set_option.argtypes = [vp, cint, ctypes.c_longlong]
+    L.fse_weight_table.argtypes = [vp, cint, ctypes.c_float, ctypes.c_float, cint, vp, vp]
     L.fse_copy_work.argtypes = [vp, cint, vp, cint, vp]
     L.fse_copy_trace.argtypes = [vp, cint, vp, vp]
     L.fse_last_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
@@ -340,6 +343,15 @@ class Context:
         _check(lib().fse_ctx_set_option(self.handle, int(option), int(value)),
                "fse_ctx_set_option")
 
+    def fse_weight_table(self, key: int, rho: float, delta: float, builder: int, dst,
+                         stream=None) -> None:
+        """W table of class pattern `key` into the device tensor dst (float32,
+        71 x 64 x 4 elements); builder 1 = FP32 split DFTs, 2 = tensor cores."""
+        _check(lib().fse_weight_table(self.handle, int(key), float(rho), float(delta),
+                                      int(builder), ctypes.c_void_p(dst.data_ptr()),
+                                      ctypes.c_void_p(_stream_handle(stream))),
+               "fse_weight_table")
+
     def fse_recent_kernel_ms(self, n: int):
         """Kernel times (ms) of the last n batches, most recent first."""
         buf = (ctypes.c_float * max(n, 1))()
@@ -353,6 +365,13 @@ class Context:
         _check(lib().fse_last_batch_config(self.handle, ctypes.byref(a), ctypes.byref(b)),
                "fse_last_batch_config")
         return {"executor": a.value, "ctas_per_sm": b.value}
+
+    def fse_last_batch_shape(self):
+        v = [ctypes.c_int() for _ in range(5)]
+        _check(lib().fse_last_batch_shape(self.handle, *[ctypes.byref(x) for x in v]),
+               "fse_last_batch_shape")
+        return dict(zip(("executor", "ctas_per_sm", "claim_order", "threads_per_cta",
+                         "blocks_per_cta"), (x.value for x in v)))
 
     def fse_last_batch_info(self):
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

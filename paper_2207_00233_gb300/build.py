@@ -22,7 +22,8 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["fse_kernels.cu", "fse_noalloc.cu", "fse_peaks.cu", "fse_loopbench.cu"]
+CU_SOURCES = ["fse_kernels.cu", "fse_noalloc.cu", "fse_peaks.cu", "fse_loopbench.cu",
+              "fse_wtable_tc.cu"]
 CPP_SOURCES = ["fse_api.cpp", "fse_hostbatch.cpp", "fse_serve.cpp", "fse_plan.cpp", "fse_sched.cpp"]
 HEADERS = ["fse_internal.h", "fse_ctx.h", "fse_iter.cuh"]
 

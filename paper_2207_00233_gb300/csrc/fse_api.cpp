@@ -638,10 +638,14 @@ int plan_frames(fse_ctx *ctx, int n, const fse_params *p, Batch &b) {
 
 // Work items: the persistent CTAs' claim order (delayed height order), one
 // launch per dependency level, or one launch per plan group.
-void claim_order(fse_ctx *ctx, int n, bool persistent, int grid, Batch &b) {
+void claim_order(fse_ctx *ctx, int n, bool persistent, int grid, int claim, Batch &b) {
     b.items.clear();
     b.level_start.clear();
-    if (persistent) {
+    if (persistent && claim == FSE_CLAIM_HEIGHT) {
+        height_claims(b.depths, b.items);
+    } else if (persistent && claim == FSE_CLAIM_LIST) {
+        schedule_claims(b.depths, std::max(grid, 1), b.items);
+    } else if (persistent) {
         delay_claims(b.depths, std::max(grid, 1), b.items,
                      [&](int m, const std::function<void(int)> &fn) { ctx->pool.run(m, fn); });
     } else if (ctx->group_launches) {
@@ -673,12 +677,13 @@ int wtables_for_batch(fse_ctx *ctx, Workspace &ws, const fse_params *p, const fl
     std::lock_guard<std::mutex> lk(ctx->wt_mu);
     fse_ctx::WTableSet *set = nullptr;
     for (auto &t : ctx->wsets)
-        if (t.rho == p->rho && t.delta == p->delta) set = &t;
+        if (t.rho == p->rho && t.delta == p->delta && t.builder == ctx->w_tables) set = &t;
     if (!set) {
         ctx->wsets.emplace_back();
         set = &ctx->wsets.back();
         set->rho = p->rho;
         set->delta = p->delta;
+        set->builder = ctx->w_tables;
         set->slot.assign(kWKeys, -1);
     }
     constexpr int kChunk = 32;  // tables per chunk
@@ -724,9 +729,24 @@ int wtables_for_batch(fse_ctx *ctx, Workspace &ws, const fse_params *p, const fl
         CK(cudaMemcpyAsync(ws.wfill.ptr, hs, kbytes + sizeof(uint64_t) * nk,
                            cudaMemcpyHostToDevice, stream));
         const char *df = static_cast<const char *>(ws.wfill.ptr);
-        CK(launch_wtables(reinterpret_cast<const int32_t *>(df),
-                          reinterpret_cast<const uint64_t *>(df + kbytes), (int)nk, p->delta,
-                          rho_tab, static_cast<const float2 *>(ctx->tw_dev.ptr), stream));
+        const int32_t *dkeys = reinterpret_cast<const int32_t *>(df);
+        const uint64_t *ddst = reinterpret_cast<const uint64_t *>(df + kbytes);
+        if (ctx->w_tables == 2) {
+            if (!ctx->wt_image.ptr) {
+                std::vector<float> img;
+                wtable_tc_image(img);
+                if ((rc = ctx->dev_reserve(ctx->wt_image, sizeof(float) * img.size()))) return rc;
+                CK(cudaMemcpy(ctx->wt_image.ptr, img.data(), sizeof(float) * img.size(),
+                              cudaMemcpyHostToDevice));
+            }
+            int *status = static_cast<int *>(ws.status.ptr);
+            CK(launch_wtables_tc(dkeys, ddst, (int)nk, p->delta, rho_tab,
+                                 static_cast<const float4 *>(ctx->wt_image.ptr), status + 1,
+                                 stream));
+        } else {
+            CK(launch_wtables(dkeys, ddst, (int)nk, p->delta, rho_tab,
+                              static_cast<const float2 *>(ctx->tw_dev.ptr), stream));
+        }
         if (!ctx->wt_fill) CK(cudaEventCreateWithFlags(&ctx->wt_fill, cudaEventDisableTiming));
         CK(cudaEventRecord(ctx->wt_fill, stream));
         // the staging is reused by the next fill of this workspace
@@ -791,7 +811,8 @@ int upload_batch(fse_ctx *ctx, Workspace &ws, int n, bool persistent, cudaStream
 
 int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
                    const fse_params *p, cudaStream_t stream,
-                   const std::vector<std::vector<uint8_t>> *host_lost, int ctas_per_sm) {
+                   const std::vector<std::vector<uint8_t>> *host_lost, int ctas_per_sm,
+                   int claim) {
     int rc = FSE_OK;
     const float *rho_tab = ctx->rho_table(p->rho, p->block, &rc);
     if (!rho_tab) return rc;
@@ -819,13 +840,18 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
     }
     ws.executor = p->executor;
     ws.ctas_per_sm = per_sm;
-    claim_order(ctx, n, persistent, grid, b);
+    if (claim < 0) claim = ctx->claim_order;
+    ws.claim = persistent ? claim : 0;
+    claim_order(ctx, n, persistent, grid, claim, b);
     const size_t n_items = b.items.size();
     int stuck_item = -1;
     if (persistent && ctx->test_stuck_dep && n_items > 0) {
         stuck_item = (int)n_items - 1;  // waits on a flag nothing sets
         ctx->test_stuck_dep = false;
     }
+    // status words of this batch (work counter, error) start at zero before
+    // its first launch, the table fill included
+    if (n_items > 0) CK(cudaMemsetAsync(ws.status.ptr, 0, sizeof(int) * 2, stream));
     if ((rc = wtables_for_batch(ctx, ws, p, rho_tab, stream, b))) return rc;
     if ((rc = upload_batch(ctx, ws, n, persistent, stream, b))) return rc;
 
@@ -851,7 +877,6 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
             CK(cudaEventCreate(&ws.k_begin[kslot]));
             CK(cudaEventCreate(&ws.k_end[kslot]));
         }
-        CK(cudaMemsetAsync(status, 0, sizeof(int) * 2, stream));
         CK(cudaEventRecord(ws.k_begin[kslot], stream));
         if (persistent) {
             WorkQueue wq;
@@ -1025,6 +1050,7 @@ extern "C" void fse_ctx_destroy(fse_ctx *ctx) {
     for (auto &e : ctx->rho_tabs) ctx->dev_release(e.second);
     for (auto &f : ctx->frags) ctx->dev_release(f);
     for (auto &c : ctx->wchunks) ctx->dev_release(c);
+    ctx->dev_release(ctx->wt_image);
     if (ctx->wt_fill) cudaEventDestroy(ctx->wt_fill);
     delete ctx;
 }
@@ -1043,13 +1069,19 @@ static int autotuned_batch(fse_ctx *ctx, const fse_frame *frames, int n,
     fse_params p = *params;
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) {
-        p.executor = it->second.first;
-        return run_batch(ctx, ctx->ws, frames, n, &p, stream, nullptr, it->second.second);
+        p.executor = it->second[0];
+        return run_batch(ctx, ctx->ws, frames, n, &p, stream, nullptr, it->second[1],
+                         it->second[2]);
     }
-    std::vector<std::pair<int, int>> cand;
+    // candidates (executor, CTAs per SM, claim order): the persistent launch
+    // with every residency and claim order, and one launch per dependency
+    // level
+    std::vector<std::vector<int>> cand;
     const int max_per_sm = max_resident_ctas(params->iters);
-    for (int c = max_per_sm; c >= 1; --c) cand.emplace_back(FSE_EXEC_PERSISTENT, c);
-    cand.emplace_back(FSE_EXEC_GROUPS, 0);
+    for (int c = max_per_sm; c >= 1; --c)
+        for (int o : {FSE_CLAIM_DELAYED, FSE_CLAIM_HEIGHT, FSE_CLAIM_LIST})
+            cand.push_back({FSE_EXEC_PERSISTENT, c, o});
+    cand.push_back({FSE_EXEC_GROUPS, 0, 0});
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
@@ -1057,19 +1089,20 @@ static int autotuned_batch(fse_ctx *ctx, const fse_frame *frames, int n,
         return FSE_ECUDA;
     }
     float best = -1.f;
-    std::pair<int, int> choice = cand.front();
+    std::vector<int> choice = cand.front();
     int rc = FSE_OK;
-    p.executor = cand.front().first;  // untimed pass
-    rc = run_batch(ctx, ctx->ws, frames, n, &p, stream, nullptr, cand.front().second);
+    p.executor = cand.front()[0];  // untimed pass
+    rc = run_batch(ctx, ctx->ws, frames, n, &p, stream, nullptr, cand.front()[1],
+                   cand.front()[2]);
     if (!rc) rc = read_status(ctx, ctx->ws, stream);
     for (size_t k = 0; k < 2 * cand.size() && !rc; ++k) {
         const auto &c = cand[k % cand.size()];
-        p.executor = c.first;
+        p.executor = c[0];
         if (cudaEventRecord(e0, stream) != cudaSuccess) {
             rc = FSE_ECUDA;
             break;
         }
-        rc = run_batch(ctx, ctx->ws, frames, n, &p, stream, nullptr, c.second);
+        rc = run_batch(ctx, ctx->ws, frames, n, &p, stream, nullptr, c[1], c[2]);
         if (!rc) rc = read_status(ctx, ctx->ws, stream);
         if (rc) break;
         float ms = 0.f;
@@ -1090,8 +1123,9 @@ static int autotuned_batch(fse_ctx *ctx, const fse_frame *frames, int n,
     ctx->tuned[key] = choice;
     // the last candidate's output stands (every candidate gives the same
     // bytes); report the chosen configuration
-    ctx->ws.executor = choice.first;
-    ctx->ws.ctas_per_sm = choice.second;
+    ctx->ws.executor = choice[0];
+    ctx->ws.ctas_per_sm = choice[1];
+    ctx->ws.claim = choice[2];
     return FSE_OK;
 }
 
@@ -1114,6 +1148,7 @@ extern "C" int fse_conceal_batch(fse_ctx *ctx, const fse_frame *frames, int n,
     ctx->last_launches = ctx->ws.launches;
     ctx->last_executor = ctx->ws.executor;
     ctx->last_ctas = ctx->ws.ctas_per_sm;
+    ctx->last_claim = ctx->ws.claim;
     return rc;
 }
 
@@ -1151,6 +1186,19 @@ extern "C" int fse_last_batch_config(fse_ctx *ctx, int *executor, int *ctas_per_
     std::lock_guard<std::mutex> lk(ctx->api_mu);
     if (executor) *executor = ctx->last_executor;
     if (ctas_per_sm) *ctas_per_sm = ctx->last_ctas;
+    return FSE_OK;
+}
+
+extern "C" int fse_last_batch_shape(fse_ctx *ctx, int *executor, int *ctas_per_sm,
+                                    int *claim_order, int *threads_per_cta,
+                                    int *blocks_per_cta) {
+    if (!ctx) return FSE_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    if (executor) *executor = ctx->last_executor;
+    if (ctas_per_sm) *ctas_per_sm = ctx->last_ctas;
+    if (claim_order) *claim_order = ctx->last_claim;
+    if (threads_per_cta) *threads_per_cta = kThreads;
+    if (blocks_per_cta) *blocks_per_cta = 1;
     return FSE_OK;
 }
 
@@ -1209,6 +1257,50 @@ extern "C" int fse_copy_trace(fse_ctx *ctx, int frame, int16_t *dst, void *cuda_
     return FSE_OK;
 }
 
+extern "C" int fse_weight_table(fse_ctx *ctx, int key, float rho, float delta, int builder,
+                                void *dst, void *cuda_stream) {
+    if (!ctx || !dst || key < 0 || key >= kWKeys || !(rho > 0.f && rho < 1.f) ||
+        !(delta >= 0.f && delta <= 1.f) || (builder != 1 && builder != 2) ||
+        (reinterpret_cast<uintptr_t>(dst) & 15))
+        return FSE_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    cudaSetDevice(ctx->device);
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    int rc = FSE_OK;
+    const float *rho_tab = ctx->rho_table(rho, kBlock, &rc);
+    if (!rho_tab) return rc;
+    Workspace &ws = ctx->ws;
+    if ((rc = ctx->dev_reserve(ws.wfill, 32)) || (rc = ctx->dev_reserve(ws.status, sizeof(int) * 4)))
+        return rc;
+    const uint64_t d = reinterpret_cast<uint64_t>(dst);
+    int32_t hk[4] = {key, 0, 0, 0};
+    char *df = static_cast<char *>(ws.wfill.ptr);
+    CK(cudaMemcpyAsync(df, hk, 16, cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(df + 16, &d, 8, cudaMemcpyHostToDevice, stream));
+    int *status = static_cast<int *>(ws.status.ptr);
+    CK(cudaMemsetAsync(status, 0, sizeof(int) * 2, stream));
+    if (builder == 2) {
+        if (!ctx->wt_image.ptr) {
+            std::vector<float> img;
+            wtable_tc_image(img);
+            if ((rc = ctx->dev_reserve(ctx->wt_image, sizeof(float) * img.size()))) return rc;
+            CK(cudaMemcpy(ctx->wt_image.ptr, img.data(), sizeof(float) * img.size(),
+                          cudaMemcpyHostToDevice));
+        }
+        CK(launch_wtables_tc(reinterpret_cast<const int32_t *>(df),
+                             reinterpret_cast<const uint64_t *>(df + 16), 1, delta, rho_tab,
+                             static_cast<const float4 *>(ctx->wt_image.ptr), status + 1, stream));
+    } else {
+        CK(launch_wtables(reinterpret_cast<const int32_t *>(df),
+                          reinterpret_cast<const uint64_t *>(df + 16), 1, delta, rho_tab,
+                          static_cast<const float2 *>(ctx->tw_dev.ptr), stream));
+    }
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, status + 1, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    return err ? FSE_ETIMEDOUT : FSE_OK;
+}
+
 extern "C" int fse_ctx_set_option(fse_ctx *ctx, int option, long long value) {
     if (!ctx) return FSE_EINVAL;
     switch (option) {
@@ -1236,8 +1328,14 @@ extern "C" int fse_ctx_set_option(fse_ctx *ctx, int option, long long value) {
         ctx->max_batch = (int)value;
         return FSE_OK;
     }
+    case FSE_OPT_CLAIM_ORDER: {
+        if (value < FSE_CLAIM_DELAYED || value > FSE_CLAIM_LIST) return FSE_EINVAL;
+        std::lock_guard<std::mutex> lk(ctx->api_mu);
+        ctx->claim_order = (int)value;
+        return FSE_OK;
+    }
     case FSE_OPT_W_TABLES: {
-        if (value != 0 && value != 1) return FSE_EINVAL;
+        if (value < 0 || value > 2) return FSE_EINVAL;
         std::lock_guard<std::mutex> lk(ctx->wt_mu);
         ctx->w_tables = (int)value;
         return FSE_OK;

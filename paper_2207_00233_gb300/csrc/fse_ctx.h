@@ -58,7 +58,7 @@ struct Workspace {
     bool k_timed = false;  // the last batch recorded a pair
     bool status_live = false;      // status word of the last launch pending
     int lost_blocks = 0, groups = 0, launches = 0;  // of the last batch
-    int executor = 0, ctas_per_sm = 0;              // its launch configuration
+    int executor = 0, ctas_per_sm = 0, claim = 0;   // its launch configuration
     std::vector<int16_t *> trace_ptr;               // per frame of the last batch
     std::vector<size_t> trace_len;
     std::vector<float *> work_ptr;
@@ -151,17 +151,19 @@ struct fse_ctx {
     bool group_launches = false;  // groups executor: one launch per plan group
     bool autotune = false;        // choose the launch configuration per shape
     bool inputs_ready = false;    // masks complete at the call (plan ahead)
-    // autotuned (executor, CTAs per SM) per batch shape
-    std::map<std::vector<long long>, std::pair<int, int>> tuned;
-    int last_executor = 0, last_ctas = 0;  // configuration of the last batch
+    int claim_order = 0;          // FSE_OPT_CLAIM_ORDER of the persistent executor
+    // autotuned (executor, CTAs per SM, claim order) per batch shape
+    std::map<std::vector<long long>, std::vector<int>> tuned;
+    int last_executor = 0, last_ctas = 0, last_claim = 0;  // configuration of the last batch
 
-    // Weight-spectrum tables per (rho, delta): slot[key] indexes addr, the
+    // Weight-spectrum tables per (rho, delta, builder): slot[key] indexes addr, the
     // device address of the key's table (-1: none yet).  Tables live in
     // chunks that are never moved or freed before the context is destroyed,
     // so batches in flight on other streams keep valid addresses.  wt_fill
     // is recorded after every fill; a batch that uses tables waits for it.
     struct WTableSet {
         float rho = 0.f, delta = 0.f;
+        int builder = 0;  // FSE_OPT_W_TABLES value that filled them
         std::vector<int32_t> slot;
         std::vector<uint64_t> addr;
     };
@@ -170,7 +172,8 @@ struct fse_ctx {
     int wchunk_used = 0;            // tables in the last chunk
     cudaEvent_t wt_fill = nullptr;
     std::mutex wt_mu;
-    int w_tables = 1;               // FSE_OPT_W_TABLES
+    int w_tables = 2;               // FSE_OPT_W_TABLES: 0 off, 1 FP32, 2 tensor cores
+    fse::DevBuf wt_image;           // constant operands of the tensor-core tables
 
     fse::DevBuf tw_dev;                                   // 64 twiddles
     std::vector<std::pair<float, fse::DevBuf>> rho_tabs;  // Eq. (2) decay per (rho, block)
@@ -226,9 +229,11 @@ constexpr uint8_t kLostPart = 1, kLostWhole = 2;
 std::vector<uint8_t> host_block_loss(const fse_frame &f, int B);
 // ctas_per_sm: persistent CTAs per SM for this batch (< 0: the context's
 // FSE_OPT_PERSISTENT_CTAS setting).
+// claim: the persistent executor's claim order (< 0: FSE_OPT_CLAIM_ORDER).
 int run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
               const fse_params *p, cudaStream_t stream,
-              const std::vector<std::vector<uint8_t>> *host_lost, int ctas_per_sm = -1);
+              const std::vector<std::vector<uint8_t>> *host_lost, int ctas_per_sm = -1,
+              int claim = -1);
 int read_status(fse_ctx *ctx, Workspace &ws, cudaStream_t stream);
 void release_workspace(fse_ctx *ctx, Workspace &ws);
 void release_host_batches(fse_ctx *ctx);

@@ -105,6 +105,7 @@ int enqueue(fse_ctx *ctx, const fse_frame *frames, int n, const fse_params *para
     ctx->last_launches = ctx->ws.launches;
     ctx->last_executor = ctx->ws.executor;
     ctx->last_ctas = ctx->ws.ctas_per_sm;
+    ctx->last_claim = ctx->ws.claim;
     if (rc) return rc;
     // the launch's status word, read back in stream order (the slot's
     // previous batch has finished, so its word is free)

@@ -154,6 +154,15 @@ constexpr int kWKeys = 1 << 16;
 // in-kernel projection): keys [n] (device), dst [n] table addresses (device).
 cudaError_t launch_wtables(const int32_t *keys, const uint64_t *dst, int n, float delta,
                            const float *rho_tab, const float2 *tw_tab, cudaStream_t stream);
+// The same tables as two DFT-as-GEMM stages on the tcgen05 tensor cores with
+// split-TF32 operands and FP32 accumulation (fse_wtable_tc.cu); image: the
+// constant DFT operands (wtable_tc_image, uploaded once); error: status word
+// for a product that did not complete in time.
+void wtable_tc_image(std::vector<float> &img);
+int wtable_tc_image_floats();
+cudaError_t launch_wtables_tc(const int32_t *keys, const uint64_t *dst, int n, float delta,
+                              const float *rho_tab, const float4 *image, int *error,
+                              cudaStream_t stream);
 
 // Work of the persistent executor: items are (frame, block) pairs in a claim
 // order in which every block follows its dependencies (the earlier-group lost

@@ -92,20 +92,32 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, uint64_t src, uint32_t b
 constexpr unsigned long long kStageLimitNs = 2000000000ull;
 
 // Copies a weight-spectrum table (kW4Bytes, W4 layout) into the W4 region
-// with one bulk copy on the CTA's staging mbarrier (initialised, its next
-// phase parity at kMbarOff + 8).  All threads call it after a barrier that
-// ends every use of the region.  Returns false on every thread when the copy
-// did not complete within kStageLimitNs; the copy in flight is then waited
-// for once more, so that it does not land after the caller moves on.
-__device__ __forceinline__ bool load_wtable(unsigned char *smem, uint64_t table) {
+// with two bulk copies on the CTA's staging mbarrier (initialised, its next
+// phase parity at kMbarOff + 8): wtable_begin (called by every thread after
+// a barrier that ends the use of the region from kWTableSplit up) copies
+// that upper part, wtable_finish (after a barrier that ends every use of the
+// region) the part below and waits for both.  wtable_finish returns false
+// on every thread when the copies did not complete within kStageLimitNs;
+// they are then waited for once more, so that they do not land after the
+// caller moves on.
+constexpr int kWTableSplit = 18 * kDft * 16;  // W4 rows 0..17 below, 18..70 above
+__device__ __forceinline__ void wtable_begin(unsigned char *smem, uint64_t table) {
+    if (threadIdx.x == 0) {
+        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(smem + kMbarOff);
+        // the region's earlier generic accesses come before the async copy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(bar, kW4Bytes);
+        bulk_load((uint32_t)__cvta_generic_to_shared(smem + kWTableSplit), table + kWTableSplit,
+                  kW4Bytes - kWTableSplit, bar);
+    }
+}
+__device__ __forceinline__ bool wtable_finish(unsigned char *smem, uint64_t table) {
     const uint32_t bar = (uint32_t)__cvta_generic_to_shared(smem + kMbarOff);
     volatile uint32_t *phase = reinterpret_cast<volatile uint32_t *>(smem + kMbarOff + 8);
     const uint32_t ph = *phase;
     if (threadIdx.x == 0) {
-        // the region's earlier generic accesses come before the async copy
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive_expect_tx(bar, kW4Bytes);
-        bulk_load((uint32_t)__cvta_generic_to_shared(smem), table, kW4Bytes, bar);
+        bulk_load((uint32_t)__cvta_generic_to_shared(smem), table, kWTableSplit, bar);
     }
     const bool ok = __syncthreads_and(mbar_wait(bar, ph, kStageLimitNs));
     if (!ok) mbar_wait(bar, ph, kStageLimitNs);
@@ -292,6 +304,8 @@ __device__ __forceinline__ void real_cols(const float2 *xr, int w, int r, float 
 // mirrored column repeats the partner entry's arithmetic exactly.
 constexpr int kTsStride = 132;
 constexpr int kXrOff = kHalfCols * kTsStride * 4;  // after ts of the x input
+// (with a W table, step 2 reads only ts of w f and its real columns, below
+// kWTableSplit = 18432 bytes: 17,952 bytes)
 static_assert(kXrOff % 16 == 0 && kXrOff + 2 * 2 * kHalfCols * 8 <=
                                        kXTileOff + 2 * kArea * kTileStride * 4,
               "column-DFT scratch must fit the area tiles");
@@ -384,10 +398,17 @@ __device__ __forceinline__ void col_dft_step2(const float *ts, const float2 *tw,
 // kW: also the spectrum of w (wre, wim and the real columns of W at
 // kXrwOff); without it only R_w, for a block whose W comes from a table
 // (the rows of w f take the same arithmetic either way).
-template <bool kW>
+// mid() runs on every thread after the barrier that ends the column DFTs'
+// first step, when only the column intermediates of w f (below kWTableSplit
+// bytes) are still to be read.
+struct NoMid {
+    __device__ void operator()() const {}
+};
+template <bool kW, class Mid = NoMid>
 __device__ __forceinline__ void project_fp32(unsigned char *smem, const float2 *tw,
                                              u64 (&rre)[8], u64 (&rim)[8],
-                                             float (&wre)[8][2], float (&wim)[8][2]) {
+                                             float (&wre)[8][2], float (&wim)[8][2],
+                                             Mid mid = Mid()) {
     constexpr int kRows = kW ? kYRows : kArea;  // rows of the row DFTs
     const float *xt = reinterpret_cast<const float *>(smem + kXTileOff);
     const float *wt = reinterpret_cast<const float *>(smem + kWTileOff);
@@ -478,6 +499,7 @@ __device__ __forceinline__ void project_fp32(unsigned char *smem, const float2 *
         if (kW) col_dft_real(yw, reinterpret_cast<float2 *>(smem + kXrwOff), tw, tid);
     }
     __syncthreads();
+    mid();
     {
         float ar[8][2], ai[8][2];
         col_dft_step2(tsx, tw, w, l, ar, ai);
@@ -847,6 +869,9 @@ __device__ __forceinline__ void store_w4(unsigned char *smem, const float (&wre)
     }
 }
 
+static_assert(kXrOff + 2 * kHalfCols * 8 <= kWTableSplit,
+              "the x-only second column step reads below the table's upper part");
+
 // The full per-block computation.  Returns the model value of this thread's
 // sample of the centre block (unclamped).
 template <int P, bool kTrace, class Src>
@@ -874,9 +899,12 @@ __device__ __forceinline__ float run_block(const Src &src, const KParams &kp,
         // computed here
         const uint64_t wtab = ((smem_addr(smem) & 127u) == 0u) ? src.table() : 0ull;
         if (wtab) {
-            project_fp32<false>(smem, tw, rre, rim, wre, wim);
+            // the upper part of the table is copied in while the column
+            // DFTs' second step still reads the lower part of the region
+            project_fp32<false>(smem, tw, rre, rim, wre, wim,
+                                [&] { wtable_begin(smem, wtab); });
             __syncthreads();  // all reads of the projection scratch are done
-            if (!load_wtable(smem, wtab) && tid == 0 && kp.error)
+            if (!wtable_finish(smem, wtab) && tid == 0 && kp.error)
                 atomicExch(kp.error, FSE_ETIMEDOUT);
             if (tid == 0) misc[0] = reinterpret_cast<const float4 *>(smem)[0].x;  // W[0]
         } else {

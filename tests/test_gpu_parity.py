@@ -406,9 +406,9 @@ def test_autotune_same_bytes_and_cached(fse, ctx):
     ctx.fse_ctx_set_option(fse.FSE_OPT_AUTOTUNE, 1)
     try:
         out1, work1 = gpu_conceal(ctx, frames, p)
-        cfg1 = ctx.fse_last_batch_config()
+        cfg1 = ctx.fse_last_batch_shape()
         out2, work2 = gpu_conceal(ctx, frames, p)
-        cfg2 = ctx.fse_last_batch_config()
+        cfg2 = ctx.fse_last_batch_shape()
     finally:
         ctx.fse_ctx_set_option(fse.FSE_OPT_AUTOTUNE, 0)
     for a, b in zip(ref_out + ref_work, out1 + work1):
@@ -418,9 +418,32 @@ def test_autotune_same_bytes_and_cached(fse, ctx):
     assert cfg1 == cfg2
     if cfg1["executor"] == fse.FSE_EXEC_PERSISTENT:
         assert 1 <= cfg1["ctas_per_sm"] <= 3
+        assert cfg1["claim_order"] in (fse.FSE_CLAIM_DELAYED, fse.FSE_CLAIM_HEIGHT,
+                                       fse.FSE_CLAIM_LIST)
     else:
         assert cfg1["executor"] == fse.FSE_EXEC_GROUPS and cfg1["ctas_per_sm"] == 0
+    assert cfg1["threads_per_cta"] == 256 and cfg1["blocks_per_cta"] == 1
     print(cfg1)
+
+
+@pytest.mark.parametrize("claim", ["delayed", "height", "list"])
+def test_claim_orders_same_bytes(fse, ctx, claim):
+    """Every claim order of the persistent executor (the autotuner's third
+    dimension) gives the bytes of the per-level launches: a block waits only
+    for the earlier-group blocks in its area."""
+    frames = [fse_synth.random_frame(h, w, rate, s) for (h, w, rate, s) in
+              [(160, 224, 0.35, 43), (96, 96, 0.6, 44)]]
+    ref_out, ref_work = gpu_conceal(ctx, frames, _params(fse, 80, 1, "groups"))
+    mode = {"delayed": fse.FSE_CLAIM_DELAYED, "height": fse.FSE_CLAIM_HEIGHT,
+            "list": fse.FSE_CLAIM_LIST}[claim]
+    ctx.fse_ctx_set_option(fse.FSE_OPT_CLAIM_ORDER, mode)
+    try:
+        out, work = gpu_conceal(ctx, frames, _params(fse, 80, 1, "persistent"))
+        assert ctx.fse_last_batch_shape()["claim_order"] == mode
+    finally:
+        ctx.fse_ctx_set_option(fse.FSE_OPT_CLAIM_ORDER, fse.FSE_CLAIM_DELAYED)
+    for a, b in zip(ref_out + ref_work, out + work):
+        assert np.array_equal(a, b, equal_nan=True)
 
 
 def test_inputs_ready_pipelined_planning(fse, ctx):
@@ -506,9 +529,9 @@ def test_host_async_pipeline(fse, ctx):
 
 
 def test_w_tables_change_no_byte(fse, ctx):
-    """FSE_OPT_W_TABLES: blocks whose sub-area classes follow from their
+    """FSE_OPT_W_TABLES = 1: blocks whose sub-area classes follow from their
     eight neighbours take W from a per-pattern table computed once per
-    context (FP32, the blocks' own arithmetic).  Outputs and FP32 working
+    context by the blocks' own FP32 split DFTs.  Outputs and FP32 working
     values are byte-identical to every block computing W itself, for the
     first call (tables filled) and a second one (tables reused), in both
     executors; frames with partial edge blocks and pixel-granular losses mix
@@ -524,9 +547,10 @@ def test_w_tables_change_no_byte(fse, ctx):
         ctx.fse_ctx_set_option(fse.FSE_OPT_W_TABLES, 0)
         try:
             ref_out, ref_work = gpu_conceal(ctx, frames, p)
-        finally:
             ctx.fse_ctx_set_option(fse.FSE_OPT_W_TABLES, 1)
-        for _ in range(2):
-            out, work = gpu_conceal(ctx, frames, p)
-            for a, b in zip(ref_out + ref_work, out + work):
-                assert np.array_equal(a, b, equal_nan=True), ex
+            for _ in range(2):
+                out, work = gpu_conceal(ctx, frames, p)
+                for a, b in zip(ref_out + ref_work, out + work):
+                    assert np.array_equal(a, b, equal_nan=True), ex
+        finally:
+            ctx.fse_ctx_set_option(fse.FSE_OPT_W_TABLES, 2)
