@@ -47,7 +47,7 @@ FP32_LANES = 128
 # DRAM bytes (read + write) of one k_persistent<FP32> launch on this workload,
 # from the committed ncu capture of this kernel on this workload (profiles/);
 # None while the kernel differs from the captured one
-TRAFFIC_BYTES_PER_LAUNCH = None
+TRAFFIC_BYTES_PER_LAUNCH = 961_688_320  # 900.40 MB read + 61.29 MB written
 
 
 def parse():
@@ -716,6 +716,7 @@ def main():
                              executor=fse.FSE_EXEC_GROUPS, precision=fse.FSE_PREC_FP32, **PARAMS)
         ctx.fse_ctx_set_option(fse.FSE_OPT_GROUP_LAUNCHES, 1)
         ctx.fse_ctx_set_option(fse.FSE_OPT_INPUTS_READY, 0)
+        ctx.fse_ctx_set_option(fse.FSE_OPT_W_TABLES, 0)  # every block projects w too
         for t in tens[:2]:
             ctx.fse_conceal_batch([t], pp, stream)
         torch.cuda.synchronize()
@@ -728,6 +729,7 @@ def main():
         p1.record(stream)
         torch.cuda.synchronize()
         ctx.fse_ctx_set_option(fse.FSE_OPT_GROUP_LAUNCHES, 0)
+        ctx.fse_ctx_set_option(fse.FSE_OPT_W_TABLES, 2)
         plain = lost_blocks / (p0.elapsed_time(p1) / 1e3)
 
     # ---- roofline of the dominant kernel (the persistent extrapolation) ----
@@ -760,6 +762,24 @@ def main():
                 "fp32": {"achieved_tflops": flops / (k_ms / 1e3) / 1e12, "peak_tflops": fp32_peak,
                          "frac": flops / (k_ms / 1e3) / 1e12 / fp32_peak,
                          "derived_peak_tflops": derived_fp32}}
+
+    # ---- where a block's time goes: the benchmark's launch once more,
+    # untimed, with the phase clocks of every block ----
+    phases = None
+    if rank == 0:
+        ctx.fse_ctx_set_option(fse.FSE_OPT_INPUTS_READY, 0)
+        ctx.fse_ctx_set_option(fse.FSE_OPT_PHASE_CLOCKS, 1)
+        ctx.fse_conceal_batch(tens, params, stream)
+        clk_ph, nb_ph = ctx.fse_last_phase_clocks(stream)
+        ctx.fse_ctx_set_option(fse.FSE_OPT_PHASE_CLOCKS, 0)
+        tot = sum(clk_ph.values())
+        phases = {"clk_per_block": clk_ph,
+                  "share": {k: v / tot for k, v in clk_ph.items()} if tot > 0 else None,
+                  "blocks": nb_ph,
+                  "what": "mean SM clocks per block of each phase, thread 0 of its CTA, "
+                          "from the kernel's instrumented instantiation (FSE_OPT_PHASE_CLOCKS; "
+                          "three CTAs share an SM: a phase includes the issue slots the "
+                          "others take)"}
 
     # ---- the benchmark's launch once more, untimed, with selection traces:
     # frame 0's FP32 working values and trace for the parity report ----
@@ -826,6 +846,8 @@ def main():
             "roofline": roofline,
             "clocks": clk,
         }
+        if phases is not None:
+            line["phases"] = phases
         if base is not None:
             line["cpu_baseline"] = base
         # the sweeps first and the summaries last: a reader of the tail of
@@ -844,11 +866,13 @@ def main():
             line["plain_path"] = {
                 "value": plain, "unit": UNIT,
                 "what": "same frames, one fse_conceal_batch call per frame, one launch per "
-                        "processing-order group, FP32",
+                        "processing-order group, every block projecting w f and w in FP32",
                 "batched_over_plain": value / plain,
-                "claim": "the >= 5x form is the FP32 batched persistent launch (this line's "
-                         "value), at the accuracy of the parity object: no reduced-precision "
-                         "form is faster (precision_sweep)"}
+                "claim": "the >= 5x form is this line's value: the batched persistent launch "
+                         "with W from tensor-core tables (TF32 parts, FP32 accumulation) and "
+                         "FP32 iterations, at the accuracy of the parity object; the single-"
+                         "pass reduced-precision projections are neither faster nor as "
+                         "accurate (precision_sweep, precision_vs_oracle)"}
         if "parity" in extra:
             line["parity"] = extra["parity"]
         print(json.dumps(line), flush=True)

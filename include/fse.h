@@ -313,6 +313,19 @@ int fse_last_batch_config(fse_ctx *ctx, int *executor, int *ctas_per_sm);
 int fse_last_batch_shape(fse_ctx *ctx, int *executor, int *ctas_per_sm, int *claim_order,
                          int *threads_per_cta, int *blocks_per_cta);
 
+/* Where a block's time goes (tracing; no counterpart in the paper): with
+ * FSE_OPT_PHASE_CLOCKS set, the persistent executor records the SM clock of
+ * its first thread at the phase boundaries of every block, and this call
+ * returns, for the last synchronous persistent batch, the mean SM clocks per
+ * block of each phase: clk[0] dependency wait, [1] TMA staging of the area,
+ * [2] gather (classes, weights), [3] projection (and W: copied from its
+ * table or computed), [4] the K iterations, [5] synthesis, [6] store and
+ * release (n values, at most 7).  Three blocks share an SM, so a phase's
+ * clocks include the issue slots other blocks take.  *blocks receives the
+ * blocks averaged (0: nothing recorded).  Synchronises `cuda_stream`.
+ * Errors: FSE_EINVAL, FSE_ECUDA. */
+int fse_last_phase_clocks(fse_ctx *ctx, void *cuda_stream, double *clk, int n, int *blocks);
+
 /* Device time of the extrapolation launches of the last fse_conceal_batch
  * or fse_conceal_batch_host call (the persistent kernel, or all group
  * launches), from CUDA events recorded on the call's stream around them.
@@ -445,6 +458,11 @@ int fse_weight_table(fse_ctx *ctx, int key, float rho, float delta, int builder,
  *                            dependencies' round; FSE_CLAIM_HEIGHT the
  *                            longest chain first; FSE_CLAIM_LIST a list
  *                            schedule of rounds of ready blocks.
+ *   FSE_OPT_PHASE_CLOCKS     1: the persistent executor records the phase
+ *                            clocks of every block (fse_last_phase_clocks;
+ *                            FP32 projections only; an instrumented build of
+ *                            the kernel, not the one that serves requests);
+ *                            0 (default): it does not.
  *   FSE_OPT_W_TABLES         blocks whose sub-area classes are fixed by
  *                            their eight neighbours (16x16 blocks lost as a
  *                            whole, FP32 projection) take the spectrum of
@@ -471,6 +489,7 @@ int fse_weight_table(fse_ctx *ctx, int key, float rho, float delta, int builder,
 #define FSE_OPT_SERVE_LATENCY_MS 10
 #define FSE_OPT_W_TABLES 11
 #define FSE_OPT_CLAIM_ORDER 12
+#define FSE_OPT_PHASE_CLOCKS 13
 #define FSE_CLAIM_DELAYED 0
 #define FSE_CLAIM_HEIGHT 1
 #define FSE_CLAIM_LIST 2

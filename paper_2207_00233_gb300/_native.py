@@ -25,12 +25,13 @@ EXPORTED = [
     "fse_plan_order", "fse_plan_claims", "fse_ctx_create", "fse_ctx_destroy", "fse_conceal_batch",
     "fse_conceal_batch_host", "fse_conceal_batch_host_async", "fse_wait_batch",
     "fse_extrapolate_areas", "fse_submit", "fse_poll",
-    "fse_drain", "fse_last_batch_info", "fse_last_batch_config", "fse_last_batch_shape", "fse_ctx_set_option", "fse_copy_work", "fse_copy_trace", "fse_last_kernel_ms", "fse_recent_kernel_ms", "fse_conceal_frame_noalloc", "fse_measure_peaks", "fse_loop_microbench", "fse_weight_table", "fse_strerror",
+    "fse_drain", "fse_last_batch_info", "fse_last_batch_config", "fse_last_batch_shape", "fse_ctx_set_option", "fse_copy_work", "fse_copy_trace", "fse_last_kernel_ms", "fse_recent_kernel_ms", "fse_last_phase_clocks", "fse_conceal_frame_noalloc", "fse_measure_peaks", "fse_loop_microbench", "fse_weight_table", "fse_strerror",
 ]
 FSE_OPT_SPIN_LIMIT, FSE_OPT_PERSISTENT_CTAS, FSE_OPT_SERVE_SLOTS = 1, 2, 3
 FSE_OPT_SERVE_MAX_BATCH, FSE_OPT_TEST_STUCK_DEP, FSE_OPT_KEEP_TRACE = 4, 5, 6
 FSE_OPT_GROUP_LAUNCHES, FSE_OPT_AUTOTUNE, FSE_OPT_INPUTS_READY = 7, 8, 9
 FSE_OPT_SERVE_LATENCY_MS, FSE_OPT_W_TABLES, FSE_OPT_CLAIM_ORDER = 10, 11, 12
+FSE_OPT_PHASE_CLOCKS = 13
 FSE_CLAIM_DELAYED, FSE_CLAIM_HEIGHT, FSE_CLAIM_LIST = 0, 1, 2
 
 
@@ -97,6 +98,8 @@ def lib() -> ctypes.CDLL:
     L.fse_drain.argtypes = [vp, cint]
     L.fse_last_batch_config.argtypes = [vp, ctypes.POINTER(cint), ctypes.POINTER(cint)]
     L.fse_last_batch_shape.argtypes = [vp] + [ctypes.POINTER(cint)] * 5
+    L.fse_last_phase_clocks.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double), cint,
+                                        ctypes.POINTER(cint)]
     L.fse_recent_kernel_ms.argtypes = [vp, cint, vp, ctypes.POINTER(cint)]
     L.fse_last_batch_info.argtypes = [vp, ctypes.POINTER(cint), ctypes.POINTER(cint),
                                       ctypes.POINTER(cint)]
@@ -365,6 +368,17 @@ class Context:
         _check(lib().fse_last_batch_config(self.handle, ctypes.byref(a), ctypes.byref(b)),
                "fse_last_batch_config")
         return {"executor": a.value, "ctas_per_sm": b.value}
+
+    PHASES = ("wait", "staging", "gather", "projection", "iterations", "synthesis", "store")
+
+    def fse_last_phase_clocks(self, stream=None):
+        """Mean SM clocks per block of each phase of the last persistent batch
+        (FSE_OPT_PHASE_CLOCKS) and the number of blocks averaged."""
+        buf = (ctypes.c_double * 7)()
+        cnt = ctypes.c_int(0)
+        _check(lib().fse_last_phase_clocks(self.handle, ctypes.c_void_p(_stream_handle(stream)),
+                                           buf, 7, ctypes.byref(cnt)), "fse_last_phase_clocks")
+        return dict(zip(self.PHASES, list(buf))), cnt.value
 
     def fse_last_batch_shape(self):
         v = [ctypes.c_int() for _ in range(5)]

@@ -865,8 +865,16 @@ int fse::run_batch(fse_ctx *ctx, Workspace &ws, const fse_frame *frames, int n,
 
     // ---- extrapolation ----
     int *status = static_cast<int *>(ws.status.ptr);
+    uint32_t *clocks = nullptr;
+    ws.clock_items = 0;
+    if (persistent && ctx->phase_clocks && n_items > 0 && p->precision == FSE_PREC_FP32) {
+        if ((rc = ctx->dev_reserve(ws.clocks, sizeof(uint32_t) * kPhaseStamps * n_items)))
+            return rc;
+        clocks = static_cast<uint32_t *>(ws.clocks.ptr);
+        ws.clock_items = (int)n_items;
+    }
     const KParams kp{p->rho, p->delta, p->gamma, p->iters, frags, block_log2(p->block),
-                     status + 1};
+                     status + 1, clocks};
     const FrameDesc *fdev = static_cast<const FrameDesc *>(ws.frames.ptr);
     const float2 *tw_tab = static_cast<const float2 *>(ctx->tw_dev.ptr);
     int launches = b.map_kernel ? 1 : 0;
@@ -970,6 +978,8 @@ void fse::release_workspace(fse_ctx *ctx, Workspace &ws) {
     ctx->dev_release(ws.tmaps);
     ctx->dev_release(ws.trace);
     ctx->dev_release(ws.wptr);
+    ctx->dev_release(ws.clocks);
+    ws.clock_items = 0;
     ctx->dev_release(ws.wfill);
     ctx->host_release(ws.wstage);
     ctx->dev_release(ws.d_luma);
@@ -1202,6 +1212,29 @@ extern "C" int fse_last_batch_shape(fse_ctx *ctx, int *executor, int *ctas_per_s
     return FSE_OK;
 }
 
+extern "C" int fse_last_phase_clocks(fse_ctx *ctx, void *cuda_stream, double *clk, int n,
+                                     int *blocks) {
+    if (!ctx || !clk || n <= 0) return FSE_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    Workspace &ws = ctx->ws;
+    if (blocks) *blocks = ws.clock_items;
+    for (int k = 0; k < n; ++k) clk[k] = 0.0;
+    if (ws.clock_items <= 0) return FSE_OK;
+    cudaSetDevice(ctx->device);
+    std::vector<uint32_t> st((size_t)ws.clock_items * kPhaseStamps);
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    CK(cudaMemcpyAsync(st.data(), ws.clocks.ptr, sizeof(uint32_t) * st.size(),
+                       cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    const int phases = std::min(n, kPhaseStamps - 1);
+    for (int i = 0; i < ws.clock_items; ++i)
+        for (int k = 0; k < phases; ++k)  // 32-bit SM clock: differences modulo 2^32
+            clk[k] += (double)(uint32_t)(st[(size_t)i * kPhaseStamps + k + 1] -
+                                         st[(size_t)i * kPhaseStamps + k]);
+    for (int k = 0; k < phases; ++k) clk[k] /= ws.clock_items;
+    return FSE_OK;
+}
+
 extern "C" int fse_last_kernel_ms(fse_ctx *ctx, float *ms) {
     if (!ctx || !ms) return FSE_EINVAL;
     std::lock_guard<std::mutex> lk(ctx->api_mu);
@@ -1326,6 +1359,12 @@ extern "C" int fse_ctx_set_option(fse_ctx *ctx, int option, long long value) {
         std::lock_guard<std::mutex> lk(ctx->mu);
         if (value < 1 || value > 4096) return FSE_EINVAL;
         ctx->max_batch = (int)value;
+        return FSE_OK;
+    }
+    case FSE_OPT_PHASE_CLOCKS: {
+        if (value != 0 && value != 1) return FSE_EINVAL;
+        std::lock_guard<std::mutex> lk(ctx->api_mu);
+        ctx->phase_clocks = value != 0;
         return FSE_OK;
     }
     case FSE_OPT_CLAIM_ORDER: {

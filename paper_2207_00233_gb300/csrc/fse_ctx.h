@@ -42,6 +42,8 @@ struct HostBuf {
 struct Workspace {
     DevBuf frames, work, lost, lost_off, gob, items, done, status, trace;
     DevBuf wptr;                   // per block: address of its W table, or 0
+    DevBuf clocks;                 // phase stamps of the last persistent batch
+    int clock_items = 0;           // items stamped (0: none)
     DevBuf wfill;                  // keys and destinations of new W tables
     HostBuf wstage;                // pinned staging of wfill
     DevBuf tmaps;                  // TMA descriptors of the frames (2 per frame)
@@ -152,6 +154,7 @@ struct fse_ctx {
     bool autotune = false;        // choose the launch configuration per shape
     bool inputs_ready = false;    // masks complete at the call (plan ahead)
     int claim_order = 0;          // FSE_OPT_CLAIM_ORDER of the persistent executor
+    bool phase_clocks = false;    // FSE_OPT_PHASE_CLOCKS
     // autotuned (executor, CTAs per SM, claim order) per batch shape
     std::map<std::vector<long long>, std::vector<int>> tuned;
     int last_executor = 0, last_ctas = 0, last_claim = 0;  // configuration of the last batch

@@ -36,9 +36,13 @@ constexpr int kXrwOff = kRedOff + kRedBytes;           // W's real columns (FP32
 constexpr int kXrwBytes = 2 * 33 * 8;                  // columns k_n = 0, 32; rows 0..32
 constexpr int kListOff = kXrwOff + kXrwBytes;          // dc list, then u list
 // misc[2..3]: TMA mbarrier, misc[4]: its next phase parity, misc[5..6]: the
-// persistent executor's claimed item and wait result
+// persistent executor's claimed item and wait result; misc[8..15]: thread
+// 0's clock at the phase boundaries of the current block (kPhaseStamps)
 constexpr int kMbarOff = kRedOff + 8 * 4 + 8 * 16 + 8;
 static_assert(kMbarOff % 8 == 0 && kMbarOff + 20 <= kListOff, "mbarrier placement");
+constexpr int kPhaseStamps = 8;
+constexpr int kStampOff = kRedOff + 8 * 4 + 8 * 16 + 32;
+static_assert(kStampOff + 4 * kPhaseStamps <= kRedOff + kRedBytes, "phase stamps placement");
 inline int smem_bytes(int iters) {
     return kListOff + iters * 8 + ((iters * 2 + 15) / 16) * 16;
 }
@@ -78,6 +82,8 @@ struct KParams {
     int lb;              // log2 of the block size B; the area is (B + 32)^2
     int *error;          // status word for a failed TMA wait (group launches;
                          // null: frames are gathered with plain loads)
+    uint32_t *clocks;    // persistent executor: [items][kPhaseStamps] phase
+                         // stamps of every block (FSE_OPT_PHASE_CLOCKS), or null
 };
 
 // Block sizes: B = 16 (the 48x48 area fills the tile) or B = 8, 4, 2 with the

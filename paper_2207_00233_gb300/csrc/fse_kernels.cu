@@ -872,9 +872,23 @@ __device__ __forceinline__ void store_w4(unsigned char *smem, const float (&wre)
 static_assert(kXrOff + 2 * kHalfCols * 8 <= kWTableSplit,
               "the x-only second column step reads below the table's upper part");
 
+// Thread 0's clock at phase boundary p of the current block (kept in shared
+// memory; the instrumented persistent executor copies them out).  Phases:
+// 0 claimed, 1 dependencies ready, 2 area staged, 3 gathered, 4 projected
+// (W in place), 5 iterated, 6 synthesised, 7 stored and released.  The
+// executor that serves requests is a separate instantiation without stamps.
+template <bool kOn>
+__device__ __forceinline__ void phase_stamp(unsigned char *smem, int p) {
+    if (kOn && threadIdx.x == 0) {
+        uint32_t t;
+        asm volatile("mov.u32 %0, %%clock;" : "=r"(t));
+        reinterpret_cast<volatile uint32_t *>(smem + kStampOff)[p] = t;
+    }
+}
+
 // The full per-block computation.  Returns the model value of this thread's
 // sample of the centre block (unclamped).
-template <int P, bool kTrace, class Src>
+template <int P, bool kTrace, bool kStamps = false, class Src>
 __device__ __forceinline__ float run_block(const Src &src, const KParams &kp,
                                            const float *rho_tab, const float2 *tw_g,
                                            unsigned char *smem, const Trace &tr) {
@@ -890,6 +904,7 @@ __device__ __forceinline__ float run_block(const Src &src, const KParams &kp,
     src.gather(reinterpret_cast<float *>(smem + kXTileOff),
                reinterpret_cast<float *>(smem + kWTileOff), rho_tab, kp.delta);
     __syncthreads();
+    phase_stamp<kStamps>(smem, 3);
 
     u64 rre[8], rim[8];
     if (P == FSE_PREC_FP32) {
@@ -922,6 +937,7 @@ __device__ __forceinline__ float run_block(const Src &src, const KParams &kp,
     }
     __syncthreads();
 
+    phase_stamp<kStamps>(smem, 4);
     const float W0 = misc[0];
     const int K = (W0 > 0.f) ? kp.iters : 0;
     const float gw = kp.gamma / fmaxf(W0, 1e-30f);
@@ -958,6 +974,7 @@ __device__ __forceinline__ float run_block(const Src &src, const KParams &kp,
         }
     }
     __syncthreads();  // list complete
+    phase_stamp<kStamps>(smem, 5);
     if (kTrace && (tr.u || tr.dc)) {
         for (int it = tid; it < kp.iters; it += kThreads) {
             if (tr.u) tr.u[it] = (it < K) ? (int32_t)ul[it] : -1;
@@ -1156,7 +1173,7 @@ __device__ __forceinline__ bool wait_area(const FrameDesc &fd, int block, bool s
     return __all_sync(0xffffffffu, ok);
 }
 
-template <int P>
+template <int P, bool kStamps>
 __global__ void __launch_bounds__(kThreads, 3)
 k_persistent(const FrameDesc *frames, WorkQueue q, KParams kp, const float *rho_tab,
              const float2 *tw_tab) {
@@ -1171,6 +1188,7 @@ k_persistent(const FrameDesc *frames, WorkQueue q, KParams kp, const float *rho_
         __syncthreads();
         const int i = s_item;
         if (i >= q.n) break;
+        phase_stamp<kStamps>(smem, 0);
         if (threadIdx.x < 32) {
             const int2 item = q.items[i];
             const bool ok = wait_area(frames[item.x], item.y, i == q.stuck_item, q);
@@ -1178,6 +1196,7 @@ k_persistent(const FrameDesc *frames, WorkQueue q, KParams kp, const float *rho_
         }
         __syncthreads();
         if (!s_ok) break;
+        phase_stamp<kStamps>(smem, 1);
         float g;
         {
             const int2 item = q.items[i];
@@ -1190,8 +1209,11 @@ k_persistent(const FrameDesc *frames, WorkQueue q, KParams kp, const float *rho_
                 }
                 stage = smem + kStageLumaOff;
             }
+            phase_stamp<kStamps>(smem, 2);
             const FrameSrc src(fd, item.y, stage);
-            g = run_block<P, false>(src, kp, rho_tab, tw_tab, smem, Trace{nullptr, nullptr, nullptr});
+            g = run_block<P, false, kStamps>(src, kp, rho_tab, tw_tab, smem,
+                                             Trace{nullptr, nullptr, nullptr});
+            phase_stamp<kStamps>(smem, 6);
         }
         // Reload the item instead of keeping it live through the iterations.
         asm volatile("" ::: "memory");
@@ -1201,7 +1223,16 @@ k_persistent(const FrameDesc *frames, WorkQueue q, KParams kp, const float *rho_
         write_frame_trace(frames[item.x], item.y, kp, smem);
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) st_release_u32(frames[item.x].done + item.y, 1u);
+        if (threadIdx.x == 0) {
+            st_release_u32(frames[item.x].done + item.y, 1u);
+            if (kStamps && kp.clocks) {
+                phase_stamp<kStamps>(smem, 7);
+                const volatile uint32_t *st =
+                    reinterpret_cast<const volatile uint32_t *>(smem + kStampOff);
+                uint32_t *dst = kp.clocks + (size_t)s_item * kPhaseStamps;
+                for (int k = 0; k < kPhaseStamps; ++k) dst[k] = st[k];
+            }
+        }
     }
 }
 
@@ -1320,9 +1351,14 @@ static cudaError_t ensure_attrs(int precision) {
         cudaError_t r = cudaFuncSetAttribute(k_group<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              max_smem);
         if (r != cudaSuccess) return r;
-        r = cudaFuncSetAttribute(k_persistent<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 max_smem);
+        r = cudaFuncSetAttribute(k_persistent<P, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
         if (r != cudaSuccess) return r;
+        if (P == FSE_PREC_FP32) {
+            r = cudaFuncSetAttribute(k_persistent<FSE_PREC_FP32, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+            if (r != cudaSuccess) return r;
+        }
         r = cudaFuncSetAttribute(k_areas<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  max_smem);
         if (r != cudaSuccess) return r;
@@ -1359,7 +1395,7 @@ cudaError_t launch_build_frags(int precision, const float2 *tw, uint4 *out, cuda
 int max_resident_ctas(int iters) {
     if (ensure_attrs(FSE_PREC_FP32) != cudaSuccess) return 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent<FSE_PREC_FP32>, kThreads,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent<FSE_PREC_FP32, false>, kThreads,
                                                       smem_bytes(iters)) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
@@ -1407,10 +1443,16 @@ cudaError_t launch_persistent(const FrameDesc *frames_dev, const WorkQueue &wq,
     cudaError_t e = ensure_attrs(precision);
     if (e != cudaSuccess) return e;
     if (wq.n <= 0) return cudaSuccess;
+    if (kp.clocks) {  // phase stamps: FP32 projections only
+        if (precision != FSE_PREC_FP32) return cudaErrorInvalidValue;
+        k_persistent<FSE_PREC_FP32, true><<<grid, kThreads, smem_bytes(kp.iters), stream>>>(
+            frames_dev, wq, kp, rho_tab, tw_tab);
+        return cudaGetLastError();
+    }
     return with_precision(precision, [&](auto pc) {
         constexpr int P = decltype(pc)::value;
-        k_persistent<P><<<grid, kThreads, smem_bytes(kp.iters), stream>>>(frames_dev, wq, kp,
-                                                                          rho_tab, tw_tab);
+        k_persistent<P, false><<<grid, kThreads, smem_bytes(kp.iters), stream>>>(
+            frames_dev, wq, kp, rho_tab, tw_tab);
         return cudaGetLastError();
     });
 }

@@ -554,3 +554,25 @@ def test_w_tables_change_no_byte(fse, ctx):
                     assert np.array_equal(a, b, equal_nan=True), ex
         finally:
             ctx.fse_ctx_set_option(fse.FSE_OPT_W_TABLES, 2)
+
+
+def test_phase_clocks(fse, ctx):
+    """FSE_OPT_PHASE_CLOCKS: the persistent executor records thread 0's SM
+    clock at every phase boundary of every block; the outputs are those of
+    the run without the stamps, and the iterations dominate at K = 200."""
+    frames = fse_synth.workload_batch_1080p(1)
+    p = _params(fse, 200, 1, "persistent")
+    ref_out, ref_work = gpu_conceal(ctx, frames, p)
+    ctx.fse_ctx_set_option(fse.FSE_OPT_PHASE_CLOCKS, 1)
+    try:
+        out, work = gpu_conceal(ctx, frames, p)
+        clk, nb = ctx.fse_last_phase_clocks()
+    finally:
+        ctx.fse_ctx_set_option(fse.FSE_OPT_PHASE_CLOCKS, 0)
+    for a, b in zip(ref_out + ref_work, out + work):
+        assert np.array_equal(a, b, equal_nan=True)
+    assert nb == ctx.fse_last_batch_info()["lost_blocks"]
+    assert all(v >= 0 for v in clk.values())
+    total = sum(clk.values())
+    assert clk["iterations"] > 0.5 * total, clk
+    print({k: round(v) for k, v in clk.items()})
