@@ -47,7 +47,7 @@ FP32_LANES = 128
 # DRAM bytes (read + write) of one k_persistent<FP32> launch on this workload,
 # from the committed ncu capture of this kernel on this workload (profiles/);
 # None while the kernel differs from the captured one
-TRAFFIC_BYTES_PER_LAUNCH = 961_688_320  # 900.40 MB read + 61.29 MB written
+TRAFFIC_BYTES_PER_LAUNCH = 961_811_712  # 900.66 MB read + 61.16 MB written
 
 
 def parse():
@@ -562,7 +562,11 @@ LOOP_VARIANTS = {0: "two barriers (warp maxima, search in the winning warp)",
                  3: "two barriers, winning warp named by the warp maxima, pre-packed step",
                  4: "as 3, with the winning lane's search by match mask and selection tree",
                  5: "calibration: update only, fixed index sequence (no selection)",
-                 6: "calibration: update + warp reduction + one barrier, fixed indices"}
+                 6: "calibration: update + warp reduction + one barrier, fixed indices",
+                 7: "as 0, the winner's value by shuffles after one read of the candidates",
+                 8: "as 7, the block maximum by a shared atomic (no second reduction)",
+                 9: "as 7 with W as planes of real and imaginary parts (36 KB), 64 registers",
+                 10: "as 9 with 128 threads of 32 entries (16 rows per warp)"}
 
 
 def loop_microbench(fse, device, iters=K_ITERS, blocks_per_cta=16, variants=None,
@@ -583,7 +587,7 @@ def loop_microbench(fse, device, iters=K_ITERS, blocks_per_cta=16, variants=None
                 out[f"v{v}_c{c}"] = {"error": str(e)}
                 continue
             out[f"v{v}_c{c}"] = {"ns": ns, "clk_at_2070": ns * 2.070}
-            if v <= 4:  # the selecting forms
+            if v <= 4 or v >= 7:  # the selecting forms
                 sums.add((c, cs))
     by_c = {}
     for c, cs in sums:

@@ -98,7 +98,9 @@ typedef struct fse_params {
 /* One frame of 8-bit luma.  luma, out and loss_mask are [height][stride]
  * row-major bytes; loss_mask[y*stride+x] != 0 marks a lost sample.  out may
  * alias luma.  stride >= width.  A block is lost when any of its in-image
- * samples is lost. */
+ * samples is lost.  Limits (FSE_EINVAL beyond them): width x height <= 2^30,
+ * height x stride < 2^31 and height x (width rounded up to 32) < 2^31, so
+ * that every sample offset fits 32 bits. */
 typedef struct fse_frame {
     const uint8_t *luma;
     uint8_t *out;
@@ -187,7 +189,10 @@ int fse_measure_peaks(int device, double *smem_gbs, double *fp32_tflops);
  * with the search by a match mask and a selection tree.  All variants
  * select the same indices.  Two calibration forms make no selection (the
  * index sequence is a fixed hash of the iteration): 5 = the update alone,
- * 6 = the update with a warp reduction and one block barrier.
+ * 6 = the update with a warp reduction and one block barrier.  7 = as 0,
+ * the candidates read once after the second barrier and the winner's value
+ * taken by shuffles; 8 = as 7, the block maximum gathered by a shared
+ * atomic maximum into one word.
  * Outputs: *ns_per_block_iter = kernel time x SMs / (blocks x iters), i.e.
  * nanoseconds per block-iteration per SM; *checksum = a hash of every
  * selected index (equal across variants).

@@ -254,6 +254,8 @@ int fse::check_frame(const fse_frame &f) {
     if (f.width <= 0 || f.height <= 0 || f.stride < f.width) return FSE_EINVAL;
     if ((long long)f.width * f.height > (1LL << 30)) return FSE_EINVAL;
     if ((long long)f.height * f.stride >= (1LL << 31)) return FSE_EINVAL;  // 32-bit offsets
+    // the FP32 working frame's rows are padded to 32 samples; its offsets are 32-bit too
+    if ((long long)f.height * ((f.width + 31) & ~31) >= (1LL << 31)) return FSE_EINVAL;
     return FSE_OK;
 }
 

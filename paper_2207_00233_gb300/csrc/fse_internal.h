@@ -69,10 +69,10 @@ static_assert(kZsOff + 64 * 2 * kArea * 4 <= kW4Bytes, "row-DFT scratch overflow
 // After the iterations the W4 region holds the synthesis tables, in chunks
 // of kSynChunk iterations: P[it][i] = dc_it exp(+j 2 pi u_m (16+i) / 64) as
 // (Re, Re, -Im, -Im) and E[it][j] = exp(+j 2 pi u_n (16+j) / 64) as 16 real
-// then 16 imaginary parts; then the partial sums of the samples.
+// then 16 imaginary parts; then the eight warps' partial 16x16 sums.
 constexpr int kSynChunk = 128;
 constexpr int kSynPartOff = kSynChunk * 16 * 16 + kSynChunk * 32 * 4;
-static_assert(kSynPartOff + 2 * 128 * 8 <= kW4Bytes, "synthesis tables overflow");
+static_assert(kSynPartOff + kWarps * 256 * 4 <= kW4Bytes, "synthesis tables overflow");
 
 struct KParams {
     float rho, delta, gamma;

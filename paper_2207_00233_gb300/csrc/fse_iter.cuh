@@ -160,6 +160,70 @@ __device__ __forceinline__ void select_two_barriers(float tmx, const u64 (&rre)[
     uim = cw.z;
 }
 
+// ---- selection: two block barriers, fewer shared-memory round trips ----------
+//
+// The same selection as select_two_barriers with two of its dependent
+// shared-memory accesses replaced.  kAtomic: each warp's maximum goes into a
+// single word with a shared atomic maximum, so after the first barrier a
+// broadcast load gives the block maximum without a second reduction (two
+// words alternate by iteration parity: thread 0 clears the one the next
+// iteration uses, whose last reads came before this iteration's first
+// barrier; both start at zero).  In every form the eight candidates are read
+// once after the second barrier (lane l reads slot l mod 8) and the winner's
+// value comes from its lane by shuffles instead of a dependent load.
+template <bool kAtomic>
+__device__ __forceinline__ void select_two_barriers_v2(float tmx, const u64 (&rre)[8],
+                                                       const u64 (&rim)[8], uint32_t *smax,
+                                                       float4 *cand, int it, uint32_t &u,
+                                                       float &ure, float &uim) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const uint32_t wmx = __reduce_max_sync(0xffffffffu, __float_as_uint(tmx));
+    uint32_t estar;
+    if (kAtomic) {
+        if (l == 0) atomicMax(smax + (it & 1), wmx);
+        __syncthreads();
+        estar = smax[it & 1];
+        if (threadIdx.x == 0) smax[(it + 1) & 1] = 0u;
+    } else {
+        if (l == 0) smax[w] = wmx;
+        __syncthreads();
+        estar = __reduce_max_sync(0xffffffffu, smax[l & (kWarps - 1)]);
+    }
+    if (__any_sync(0xffffffffu, __float_as_uint(tmx) == estar)) {
+        uint32_t kk = 0xffffffffu;
+        float cre = 0.f, cim = 0.f;
+        if (__float_as_uint(tmx) == estar) {
+#pragma unroll
+            for (int r = 7; r >= 0; --r) {
+                const float2 e = unpack2(energy2(rre[r], rim[r]));
+                const float2 re = unpack2(rre[r]), im = unpack2(rim[r]);
+                if (__float_as_uint(e.y) == estar) {
+                    kk = (uint32_t)((8 * w + r) * kDft + l + 32);
+                    cre = re.y;
+                    cim = im.y;
+                }
+                if (__float_as_uint(e.x) == estar) {
+                    kk = (uint32_t)((8 * w + r) * kDft + l);
+                    cre = re.x;
+                    cim = im.x;
+                }
+            }
+        }
+        const uint32_t wk = __reduce_min_sync(0xffffffffu, kk);
+        if (kk == wk) cand[w] = make_float4(__uint_as_float(wk), cre, cim, 0.f);
+    } else if (l == 0) {
+        cand[w].x = __uint_as_float(0xffffffffu);
+    }
+    __syncthreads();
+    const float4 c = cand[l & (kWarps - 1)];
+    u = __reduce_min_sync(0xffffffffu, __float_as_uint(c.x));
+    // warp w owns the indices [512 w, 512 w + 512): the winner's slot, and
+    // the lane that read it, is u >> 9
+    const int ws = (int)((u >> 9) & (kWarps - 1));
+    ure = __shfl_sync(0xffffffffu, c.y, ws);
+    uim = __shfl_sync(0xffffffffu, c.z, ws);
+}
+
 // ---- selection: two block barriers, the winning warp named by its maximum -----
 //
 // Warp maxima -> barrier -> every warp reads the eight maxima and names the
