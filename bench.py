@@ -47,7 +47,7 @@ FP32_LANES = 128
 # DRAM bytes (read + write) of one k_persistent<FP32> launch on this workload,
 # from the committed ncu capture of this kernel on this workload (profiles/);
 # None while the kernel differs from the captured one
-TRAFFIC_BYTES_PER_LAUNCH = 961_811_712  # 900.66 MB read + 61.16 MB written
+TRAFFIC_BYTES_PER_LAUNCH = 959_958_528  # 899.08 MB read + 60.88 MB written
 
 
 def parse():
@@ -556,10 +556,11 @@ def serving_run(fse, rates=SERVE_RATES, seconds=10.0, pool=64, latency_budget_ms
     return out
 
 
-LOOP_VARIANTS = {0: "two barriers (warp maxima, search in the winning warp)",
+LOOP_VARIANTS = {0: "two barriers (warp maxima, search in the warps holding the maximum)",
                  1: "one barrier (row maxima reduced during the update)",
                  2: "one barrier (every warp searches its maximum)",
-                 3: "two barriers, winning warp named by the warp maxima, pre-packed step",
+                 3: "two barriers, winning warp named by the warp maxima, pre-packed step "
+                    "(the block kernel's form)",
                  4: "as 3, with the winning lane's search by match mask and selection tree",
                  5: "calibration: update only, fixed index sequence (no selection)",
                  6: "calibration: update + warp reduction + one barrier, fixed indices",

@@ -185,14 +185,17 @@ int fse_measure_peaks(int device, double *smem_gbs, double *fp32_tflops);
  * winning warp), 1 = one barrier (row maxima reduced during the update,
  * one candidate slot per warp), 2 = one barrier (every warp searches its
  * maximum), 3 = two barriers (the winning warp named from the warp maxima,
- * which alone searches and publishes the pre-packed update step), 4 = as 3
+ * which alone searches and publishes the pre-packed update step; the form
+ * the block kernels use), 4 = as 3
  * with the search by a match mask and a selection tree.  All variants
  * select the same indices.  Two calibration forms make no selection (the
  * index sequence is a fixed hash of the iteration): 5 = the update alone,
  * 6 = the update with a warp reduction and one block barrier.  7 = as 0,
  * the candidates read once after the second barrier and the winner's value
  * taken by shuffles; 8 = as 7, the block maximum gathered by a shared
- * atomic maximum into one word.
+ * atomic maximum into one word; 9 = as 7 with W kept once, as planes of
+ * real and imaginary parts (4 CTAs per SM fit); 10 = as 9 with 128-thread
+ * CTAs whose threads hold 32 entries.
  * Outputs: *ns_per_block_iter = kernel time x SMs / (blocks x iters), i.e.
  * nanoseconds per block-iteration per SM; *checksum = a hash of every
  * selected index (equal across variants).

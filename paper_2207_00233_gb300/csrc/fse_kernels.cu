@@ -899,7 +899,7 @@ __device__ __forceinline__ float run_block(const Src &src, const KParams &kp,
     const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
     float2 *tw = reinterpret_cast<float2 *>(smem + kTwOff);
     uint32_t *smax = reinterpret_cast<uint32_t *>(smem + kRedOff);
-    float4 *cand = reinterpret_cast<float4 *>(smem + kRedOff + 32);
+    uint4 *slot = reinterpret_cast<uint4 *>(smem + kRedOff + 32);  // the published step
     float *misc = reinterpret_cast<float *>(smem + kRedOff + 32 + 128);
     float2 *dcl = reinterpret_cast<float2 *>(smem + kListOff);
     uint16_t *ul = reinterpret_cast<uint16_t *>(smem + kListOff + kp.iters * 8);
@@ -947,26 +947,25 @@ __device__ __forceinline__ float run_block(const Src &src, const KParams &kp,
     const float gw = kp.gamma / fmaxf(W0, 1e-30f);
     const uint32_t w4addr = smem_addr(smem);
 
-    u64 ndcr2 = 0ull, dci2 = 0ull, ndci2 = 0ull;  // first pass: dc = 0
-    uint32_t wbase = w4_base(w4addr, 0, 0);
+    // Sec. 4 iterations.  Per iteration: the update with the previous
+    // coefficient (none in the first pass) and every thread's maximum
+    // energy; then the selection: the warp maxima meet at a barrier, the
+    // smallest warp holding the block maximum searches its entries for the
+    // smallest index, and its lane that holds it computes dc = gamma R_w[u] /
+    // W[0], appends (dc, u) to the lists and publishes the update step,
+    // which every thread reads after a second barrier.  (The loop
+    // microbenchmark compares this form with the alternatives.)
+    const uint32_t w8k = (uint32_t)(8 * w) << 10, l16 = (uint32_t)l << 4;
+    Step st{0ull, 0ull, 0ull, 0u, 0u};  // first pass: dc = 0
     for (int it = 0; it < K; ++it) {
-        const float tmx = update_and_max(wbase, ndcr2, dci2, ndci2, rre, rim);
-        uint32_t u;
-        float ure, uim;
-        select_two_barriers(tmx, rre, rim, smax, cand, u, ure, uim);
-        const float dcr = ure * gw, dci = uim * gw;
-        if (tid == 0) {
-            dcl[it] = make_float2(dcr, dci);
-            ul[it] = (uint16_t)u;
-        }
-        ndcr2 = pack2(-dcr, -dcr);
-        dci2 = pack2(dci, dci);
-        ndci2 = pack2(-dci, -dci);
-        wbase = w4_base(w4addr, (int)(u >> 6), (int)(u & 63));
+        const uint32_t wb = w4_addr_of(w4addr, w8k, l16, st);
+        const float tmx = update_and_max(wb, st.ndcr2, st.dci2, st.ndci2, rre, rim);
+        select_named_warp<false>(tmx, rre, rim, gw, it, smax, slot, dcl, ul, st);
     }
-
     if (kTrace && tr.r) {  // residual after the last update (inspection only)
-        if (K > 0) update_and_max(wbase, ndcr2, dci2, ndci2, rre, rim);
+        if (K > 0)
+            update_and_max(w4_addr_of(w4addr, w8k, l16, st), st.ndcr2, st.dci2, st.ndci2, rre,
+                           rim);
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             const float2 re = unpack2(rre[r]), im = unpack2(rim[r]);
