@@ -877,10 +877,10 @@ static_assert(kXrOff + 2 * kHalfCols * 8 <= kWTableSplit,
 // 0 claimed, 1 dependencies ready, 2 area staged, 3 gathered, 4 projected
 // (W in place), 5 iterated, 6 synthesised, 7 stored and released.  The
 // stamps at 3, 4 and 5 are taken in every instantiation: three shared
-// stores per block, and with them the persistent kernel measured 15.72 ms
-// against 16.02 ms on the 16-frame 1080p batch (same registers and spills;
-// the code around the iteration loop is scheduled differently).  The
-// others, and the copy-out, belong to the instrumented executor only.
+// stores per block, and with them the persistent kernel measured 1-2%
+// faster on the 16-frame 1080p batch (A/B builds; same registers and
+// spills: the code around the iteration loop is scheduled differently).
+// The others, and the copy-out, belong to the instrumented executor only.
 template <bool kOn>
 __device__ __forceinline__ void phase_stamp(unsigned char *smem, int p) {
     if (kOn && threadIdx.x == 0) {
