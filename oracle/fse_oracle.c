@@ -348,15 +348,24 @@ int oracle_extrapolate_area(int M, int N, int F, const double *f,
                 u = k;
             }
         }
-        /* Margin of the choice: |R_w[u]| minus the largest magnitude that is
-         * strictly smaller (exact ties are resolved by the index rule), in
-         * units of the scale above.  A small margin is a near-tie that a
-         * lower precision may resolve the other way. */
+        /* Margin of the choice: |R_w[u]| minus the largest magnitude among
+         * the other entries, in units of the scale above.  A small margin is
+         * a near-tie that a lower precision may resolve the other way.  An
+         * exact tie counts as margin 0 (a lower precision rounds the tied
+         * magnitudes apart), except an exact tie with the conjugate partner
+         * R_w[-u]: R_w[-u] = conj R_w[u] holds in any precision that keeps
+         * a real input's symmetry, and the index rule then decides alike. */
         if (margin_out) {
+            const size_t um = u / (size_t)F, un = u % (size_t)F;
+            const size_t up = ((F - um) % F) * (size_t)F + (F - un) % F;
             double second = -1.0;
             for (size_t k = 0; k < FF; ++k) {
+                if (k == u)
+                    continue;
                 double e = R[2 * k] * R[2 * k] + R[2 * k + 1] * R[2 * k + 1];
-                if (e < best && e > second)
+                if (k == up && e == best)
+                    continue;
+                if (e > second)
                     second = e;
             }
             margin_out[it] = (second < 0.0 || !(scale > 0.0))

@@ -40,9 +40,10 @@ void oracle_weights(int M, int N, const uint8_t *cls, double rho, double delta,
  * Optional outputs (NULL to skip): g_out [M*N] real part of the model,
  * w_out [M*N], R0_out/W_out/R_out/coef_out [F*F complex interleaved],
  * u_out [K] selected linear index F*k_m + k_n, dc_out [K complex],
- * margin_out [K]: per iteration, |R_w[u]| minus the largest strictly smaller
- * |R_w[k]|, divided by sum|w f| + W[0] * sum of the earlier |dc| (HUGE_VAL
- * when there is no competitor or no support). */
+ * margin_out [K]: per iteration, |R_w[u]| minus the largest |R_w[k]| over
+ * k != u, divided by sum|w f| + W[0] * sum of the earlier |dc| (HUGE_VAL
+ * when there is no competitor or no support); an exact tie gives 0, except
+ * an exact tie with the conjugate partner k = -u, which is skipped. */
 int oracle_extrapolate_area(int M, int N, int F, const double *f,
                             const uint8_t *cls, double rho, double delta,
                             double gamma, int K, int tie_largest,

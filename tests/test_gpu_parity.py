@@ -146,6 +146,39 @@ def test_small_frames_partial_blocks(fse, ctx, h, w, rate, seed, order):
     run_and_compare(ctx, frames, p, f"{h}x{w}")
 
 
+@pytest.mark.parametrize("h,w,kind", [(1, 1, "lost"), (5, 7, "random"), (1, 40, "random"),
+                                      (40, 1, "random"), (17, 17, "last")])
+def test_degenerate_frame_sizes(fse, ctx, h, w, kind):
+    """Frames smaller than one block, one sample high or wide, or with a
+    single lost sample in a partial corner block, in both orders, against
+    the oracle.  A lost 1x1 frame has no support at all: W[0] = 0, so no
+    iteration runs and the sample becomes 0, as in the oracle."""
+    rng = np.random.default_rng(h * 100 + w)
+    img = (rng.random((h, w)) * 255).astype(np.uint8)
+    if kind == "random":
+        mask = (rng.random((h, w)) < 0.4).astype(np.uint8)
+    elif kind == "last":
+        mask = np.zeros((h, w), np.uint8)
+        mask[-1, -1] = 1
+    else:
+        mask = np.ones((h, w), np.uint8)
+    for order in (0, 1):
+        p = _params(fse, 30, order, "persistent")
+        run_and_compare(ctx, [(img, mask)], p, f"{h}x{w} {kind} order {order}")
+
+
+def test_one_sample_frame_without_loss_unchanged(fse, ctx):
+    img = np.array([[173]], np.uint8)
+    (out,), _ = gpu_conceal(ctx, [(img, np.zeros_like(img))], _params(fse, 30, 1, "persistent"),
+                            want_work=False)
+    assert np.array_equal(out, img)
+
+
+def test_empty_batch_rejected(fse, ctx):
+    with pytest.raises(fse.FseError):
+        ctx.fse_conceal_batch([], _params(fse, 30, 1, "persistent"))
+
+
 def test_no_loss_frame(fse, ctx):
     img = fse_synth.make_image(64, 96, 7)
     mask = np.zeros_like(img)
